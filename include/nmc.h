@@ -1,0 +1,179 @@
+/*
+ * nmc.h -- C ABI of libnmc: the determinant quantum Monte Carlo (DQMC) sweep used by
+ * network-initialized Monte Carlo (arXiv 2106.00712), run on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation is the Markov chain over the discrete Hubbard-Stratonovich field s(i,l)
+ * of the half-filled Hubbard model (Eq. 3) on a periodic Lx x Ly square lattice, with
+ * weight prod_sigma Det[I + B^sigma_L ... B^sigma_1] (Supplemental Material Sec. I.2,
+ * partition function in determinant form) and B^sigma_l = e^{-dtau K} e^{sigma lam
+ * diag s(.,l)}, cosh lam = e^{dtau U/2} (Sec. I.2, discrete HS transform). One sweep gives
+ * every s(i,l) one Metropolis flip attempt (Sec. I.3, definition of a sweep); chains are
+ * independent, one per initial configuration (Algorithm 1, step 4).
+ *
+ * Conventions shared by every call
+ *  - Every call returns nmc_status; nothing aborts or throws across the ABI. On failure
+ *    nmc_last_error(ctx) holds a one-line reason (until the next failing call).
+ *  - The caller owns every buffer it passes; the library copies what it needs. The
+ *    library owns the context and all device memory it allocates (cudaMalloc).
+ *  - Device work is ordered on the context's CUDA stream (nmc_options.cuda_stream, NULL =
+ *    the legacy default stream). Calls that return host data synchronise that stream.
+ *  - A context is not thread-safe: serialise calls on one context.
+ *  - Layouts: fields are int8 [chain][l][i], l = 0..L_tau-1 the imaginary-time slice,
+ *    i = x + Lx*y the site; values +1 or -1. Matrices are row-major N x N doubles.
+ *  - Random numbers: Philox4x32-10 keyed by seed (key = low, high 32 bits), counter
+ *    (l*N + i, sweep, chain, tag); tag 0 = flip uniform u = x0 * 2^-32, accepted iff
+ *    u < |R|; tag 1 = initial field, s = -1 iff the top bit of x0 is set. "chain" is the
+ *    global chain index (local index + nmc_options.chain_offset), so results do not
+ *    depend on how chains are split over processes.
+ */
+#ifndef NMC_H
+#define NMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nmc_ctx nmc_ctx;
+
+typedef enum {
+  NMC_OK = 0,
+  NMC_EINVAL = 1,    /* invalid argument or size; nothing changed                        */
+  NMC_ENOMEM = 2,    /* device or host allocation failed                                 */
+  NMC_ECUDA = 3,     /* a CUDA call failed (no device, launch error, ...)                */
+  NMC_ENUMERIC = 4,  /* non-finite G or stabilization drift above nmc_options.drift_tol  */
+  NMC_ETIMEOUT = 5,  /* a bounded device-side wait expired                               */
+  NMC_ESTATE = 6     /* call out of order (e.g. nmc_sweep before fields are set)         */
+} nmc_status;
+
+/* Arithmetic of the propagation steps. Ratios, acceptance, UDV stabilization, the
+ * recomputed G and the measurements are always FP64. */
+typedef enum {
+  NMC_FP64 = 0,      /* flips, delayed updates and wraps in FP64                         */
+  NMC_FP32 = 1       /* flips, delayed updates and wraps in FP32 (FP32 accumulation)     */
+} nmc_precision;
+
+typedef struct {
+  int n_chains;          /* independent chains held by this context (>= 1)       default 1  */
+  int delay_k;           /* accepted flips folded per rank-k delayed update (>= 1) def. 16   */
+  int precision;         /* nmc_precision                                        default 0  */
+  double drift_tol;      /* NMC_ENUMERIC if max|G_wrapped - G_recomputed| exceeds this;
+                            <= 0 selects 1e-6 (FP64) or 1e-3 (FP32)              default 0  */
+  long long chain_offset;/* global index of local chain 0 (Philox counter word 2) def. 0   */
+  void* cuda_stream;     /* cudaStream_t for all device work                     def. NULL */
+} nmc_options;
+
+typedef struct {
+  double mean;
+  double err;            /* standard error: across chains (>= 2 chains) or over 10 bins of
+                            the per-sweep series (1 chain); 0 when not estimable          */
+} nmc_est;
+
+typedef struct {
+  nmc_est energy;        /* <H>/N of Eq. 3 (sign-weighted)                                  */
+  nmc_est ekin;          /* kinetic part: -(1/N) sum_sigma Tr(K G~^sigma)                   */
+  nmc_est double_occ;    /* (1/N) sum_i <n_i,up n_i,dn>                                    */
+  nmc_est s_pipi;        /* S(Q) at Q = (pi,pi), S(Q) as defined with Eq. 4               */
+  nmc_est density;       /* (1/N) sum_i,sigma <n_i,sigma>                                  */
+  nmc_est sign;          /* average configuration sign                                     */
+  double accept;         /* accepted / attempted flips                                     */
+  double max_drift;      /* max over stabilizations of max|G_wrapped - G_recomputed|       */
+  long long n_meas;      /* measurements accumulated (per chain)                           */
+  long long n_disagree;  /* replay sweeps: attempts whose own decision differed            */
+} nmc_obs;
+
+/* Create a context for the periodic Lx x Ly square lattice with hopping t and
+ * interaction U (Eq. 3) at inverse temperature beta, Trotter step dtau (Sec. I.2:
+ * L_tau = beta/dtau slices), stabilization every n_wrap slices, Philox seed `seed`.
+ * Host-side set-up (K, e^{-+dtau K}, e^{-+dtau K/2} by a Jacobi eigensolver, lam) happens
+ * here; device memory is allocated by nmc_configure / the first call that needs it.
+ * NMC_EINVAL: Lx*Ly < 2, Lx or Ly odd and > 1 (lattice must be bipartite), t <= 0,
+ * U < 0, beta <= 0, dtau <= 0, beta/dtau not an integer to 1e-9 relative,
+ * L_tau % n_wrap != 0, n_wrap < 1, N > 1024, out == NULL. *out is NULL on failure. */
+nmc_status nmc_create(int Lx, int Ly, double t, double U, double beta, double dtau,
+                      int n_wrap, uint64_t seed, nmc_ctx** out);
+
+/* Set options (copied). Allowed before the first nmc_set_fields / nmc_generate only
+ * (NMC_ESTATE after). opts == NULL restores the defaults. Allocates device memory:
+ * NMC_ENOMEM / NMC_ECUDA on failure. */
+nmc_status nmc_configure(nmc_ctx* ctx, const nmc_options* opts);
+
+/* Fill `opts` with the defaults listed in nmc_options. */
+void nmc_default_options(nmc_options* opts);
+
+/* Set every chain's field from host memory (int8 [n_chains][L_tau][N], n = element
+ * count, values +-1: NMC_EINVAL otherwise), then build the left UDV stack and the
+ * equal-time G_0 = (I + B_{L-1}...B_0)^{-1} of each spin. Resets acceptance counters,
+ * accumulators, drift and the sweep direction (next sweep ascends in l); the sweep
+ * counter (Philox word 1) keeps counting. */
+nmc_status nmc_set_fields(nmc_ctx* ctx, const int8_t* s, size_t n);
+
+/* As nmc_set_fields with a device pointer (read on the context stream; values are not
+ * validated -- entries other than +1 are treated as -1). */
+nmc_status nmc_set_fields_device(nmc_ctx* ctx, const int8_t* d_s, size_t n);
+
+/* Generate initial fields on the device. mode 0: uniform random from Philox (tag 1),
+ * ignoring `model`. Other modes (learned generators of Algorithm 1, step 3): NMC_EINVAL
+ * in this library version. Then as nmc_set_fields. */
+nmc_status nmc_generate(nmc_ctx* ctx, int mode, const void* model);
+
+/* Run n_sweeps sweeps on every chain (n_sweeps >= 0). Sweeps alternate direction
+ * (ascending l, then descending); within a slice sites go i = 0..N-1. G is recomputed
+ * from the UDV stacks every n_wrap slices; if measure != 0 the estimators are
+ * accumulated at each recompute on the symmetric-Trotter G~ = e^{dtau K/2} G e^{-dtau K/2}.
+ * Returns NMC_ENUMERIC if the drift is non-finite or above drift_tol (state is kept). */
+nmc_status nmc_sweep(nmc_ctx* ctx, int n_sweeps, int measure);
+
+/* One sweep that applies the given accept decisions instead of its own
+ * (uint8 [n_chains][L_tau][N], nonzero = flip; n = element count). The library still
+ * evaluates its own ratio for every attempt and counts disagreements
+ * (nmc_obs.n_disagree). Used to compare precisions on identical trajectories. */
+nmc_status nmc_sweep_replay(nmc_ctx* ctx, const uint8_t* accept, size_t n, int measure);
+
+/* Reduce the accumulators. per_chain: array of n_chains (or NULL); pooled: one (or
+ * NULL). Pooled means are averages of per-chain means; errors as in nmc_est. */
+nmc_status nmc_measure(nmc_ctx* ctx, nmc_obs* per_chain, nmc_obs* pooled);
+
+/* Copy every chain's current field to host memory (int8 [n_chains][L_tau][N]). */
+nmc_status nmc_get_fields(nmc_ctx* ctx, int8_t* s, size_t n);
+
+/* Copy the current equal-time G of one chain and spin (0 = up, 1 = down) to host
+ * memory (N x N row-major). After an even number of sweeps since the fields were set,
+ * G sits at slice 0, after an odd number at slice L_tau (equal to slice 0 cyclically).
+ * In FP32 mode the FP32 G is widened. */
+nmc_status nmc_get_green(nmc_ctx* ctx, int chain, int spin, double* G);
+
+/* Sizes: N, L_tau, n_chains, effective delay (after the shared-memory clamp). */
+nmc_status nmc_get_dims(const nmc_ctx* ctx, int* N, int* L_tau, int* n_chains, int* delay_k);
+
+/* Checkpoint: all state needed for an exact resume (fields, sweep counter, direction,
+ * accumulators, counters). buf == NULL: *n receives the size. NMC_EINVAL if *n is too
+ * small. nmc_restore rebuilds the UDV stacks from the fields. */
+nmc_status nmc_checkpoint(nmc_ctx* ctx, void* buf, size_t* n);
+nmc_status nmc_restore(nmc_ctx* ctx, const void* buf, size_t n);
+
+/* Host-only helper (no GPU needed): e^{c K} for the periodic Lx x Ly hopping matrix K
+ * (K_ij = -t on nearest neighbours), by the library's Jacobi eigensolver. out: N x N. */
+nmc_status nmc_expk(int Lx, int Ly, double t, double c, double* out);
+
+/* Host-only helper: Philox4x32-10 block function; out[4] = words of counter
+ * (c0,c1,c2,c3) under key (k0,k1). Same code as the device generator's host twin. */
+void nmc_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                uint32_t k1, uint32_t out[4]);
+
+/* Device generator check: out[4*j + w] = word w of Philox(counter (c0[j], c1, c2, c3),
+ * key (k0, k1)) for j < n, computed by the device code the sweep uses. Device out. */
+nmc_status nmc_philox_device(const uint32_t* d_c0, int n, uint32_t c1, uint32_t c2,
+                             uint32_t c3, uint32_t k0, uint32_t k1, uint32_t* d_out,
+                             void* cuda_stream);
+
+const char* nmc_last_error(const nmc_ctx* ctx);
+const char* nmc_version(void);
+void nmc_destroy(nmc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NMC_H */

@@ -1,0 +1,187 @@
+// Local Metropolis updates of one time slice with rank-k delayed Green's function updates.
+//
+// One CTA per chain handles both spins. For slice l the CTA draws the N Philox uniforms
+// u_i (counter (l*N+i, sweep, chain, 0)), then visits i = 0..N-1 in order:
+//   G^_ii = G0_ii + sum_{q<m} a_q[i] b_q[i]                    (warp 0, both spins)
+//   R^sigma = 1 + Delta^sigma (1 - G^_ii), Delta^sigma = e^{-2 sigma lam s} - 1 (FP64)
+//   accept iff u_i < |R^up R^dn|
+// and on acceptance appends the Sherman-Morrison vectors of the flip,
+//   a_m = -(Delta/R^sigma) (e_i - G^_{:,i}),   b_m = G^_{i,:},
+// each computed from G0 and the m earlier pairs (all threads). When m reaches k, or at
+// the end of the slice, the k pairs are folded into G0 as one rank-k update
+// G0 += A B^T. In exact arithmetic this equals applying each rank-1 update at once.
+// G0 of both spins sits in shared memory when it fits (N <= 64 in FP64), else in global
+// memory (L2); the panels always live in shared memory (k is clamped to fit).
+#include "nmc_internal.cuh"
+
+namespace nmc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__device__ void flush(T* G, const T* Ap, const T* Bp, int m, int N, int KK, long long NN) {
+  // G[sp][r][c] += sum_{q<m} A[sp][q][r] * B[sp][q][c]
+  for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) {
+    const int sp = (int)(e / NN);
+    const long long rc = e - sp * NN;
+    const int r = (int)(rc / N), c = (int)(rc % N);
+    const T* A_ = Ap + (long long)sp * KK * N;
+    const T* B_ = Bp + (long long)sp * KK * N;
+    T v = G[e];
+    for (int q = 0; q < m; ++q) v = fma(A_[q * N + r], B_[q * N + c], v);
+    G[e] = v;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_accept;
+  __shared__ double s_coef[2];
+  __shared__ double s_sign;
+  __shared__ unsigned long long s_cnt[3];
+
+  const int c = blockIdx.x;
+  const int N = f.N, KK = f.kk;
+  const long long NN = (long long)N * N;
+  T* Ap = (T*)smraw;                // [2][KK][N]
+  T* Bp = Ap + 2 * KK * N;          // [2][KK][N]
+  T* diag = Bp + 2 * KK * N;        // [2][N]
+  T* Gs = diag + 2 * N;             // [2][N][N] when g_in_smem
+  double* u = (double*)(((uintptr_t)(Gs + (f.g_in_smem ? 2 * NN : 0)) + 15) & ~(uintptr_t)15);
+  int8_t* sl = (int8_t*)(u + N);
+
+  T* Gg = f.G + (long long)c * 2 * NN;
+  T* G = f.g_in_smem ? Gs : Gg;
+  int8_t* fl = f.fields + ((long long)c * f.L + f.l) * N;
+  const uint32_t gchain = (uint32_t)(f.chain_offset + c);
+  const uint8_t* rp = f.replay ? f.replay + ((long long)c * f.L + f.l) * N : nullptr;
+
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    sl[i] = fl[i];
+    uint32_t ctr[4] = {(uint32_t)(f.l * N + i), f.sweep, gchain, kTagFlip};
+    philox4x32_10(ctr, f.key0, f.key1);
+    u[i] = (double)ctr[0] * 2.3283064365386962890625e-10;  // 2^-32
+  }
+  if (f.g_in_smem)
+    for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) Gs[e] = Gg[e];
+  if (threadIdx.x == 0) {
+    s_sign = f.sign[c];
+    s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+    const int sp = i / N, r = i % N;
+    diag[i] = G[sp * NN + (long long)r * N + r];
+  }
+  __syncthreads();
+
+  int m = 0;
+  for (int i = 0; i < N; ++i) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x, sp = lane >> 4, q0 = lane & 15;
+      const T* A_ = Ap + sp * KK * N;
+      const T* B_ = Bp + sp * KK * N;
+      T sum = T(0);
+      for (int q = q0; q < m; q += 16) sum = fma(A_[q * N + i], B_[q * N + i], sum);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      const T sum_dn = __shfl_sync(0xffffffffu, sum, 16);
+      if (lane == 0) {
+        const double gu = (double)(diag[i] + sum);
+        const double gd = (double)(diag[N + i] + sum_dn);
+        const int s = sl[i];
+        const double du = (s > 0) ? f.dm : f.dp;  // e^{-2 lam s} - 1
+        const double dd = (s > 0) ? f.dp : f.dm;  // e^{+2 lam s} - 1
+        const double Ru = 1.0 + du * (1.0 - gu);
+        const double Rd = 1.0 + dd * (1.0 - gd);
+        const double R = Ru * Rd;
+        const bool mine = u[i] < fabs(R);
+        bool acc = mine;
+        if (rp) {
+          acc = rp[i] != 0;
+          if (acc != mine) s_cnt[2]++;
+        }
+        s_cnt[0]++;
+        s_accept = acc ? 1 : 0;
+        if (acc) {
+          s_coef[0] = -du / Ru;
+          s_coef[1] = -dd / Rd;
+          if (R < 0.0) s_sign = -s_sign;
+          s_cnt[1]++;
+          sl[i] = (int8_t)(-s);
+        }
+      }
+    }
+    __syncthreads();
+    if (s_accept) {
+      const T coef[2] = {(T)s_coef[0], (T)s_coef[1]};
+      for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
+        const int sp = t / (2 * N);
+        const int kind = (t / N) & 1;
+        const int r = t % N;
+        const T* Gsp = G + sp * NN;
+        const T* A_ = Ap + sp * KK * N;
+        const T* B_ = Bp + sp * KK * N;
+        if (kind == 0) {  // column i of G^: a_m = coef (e_i - G^_{:,i})
+          T v = Gsp[(long long)r * N + i];
+          for (int q = 0; q < m; ++q) v = fma(A_[q * N + r], B_[q * N + i], v);
+          Ap[(sp * KK + m) * N + r] = coef[sp] * ((r == i ? T(1) : T(0)) - v);
+        } else {          // row i of G^: b_m = G^_{i,:}
+          T v = Gsp[(long long)i * N + r];
+          for (int q = 0; q < m; ++q) v = fma(A_[q * N + i], B_[q * N + r], v);
+          Bp[(sp * KK + m) * N + r] = v;
+        }
+      }
+      ++m;
+      __syncthreads();
+      if (m == KK) {
+        flush(G, Ap, Bp, m, N, KK, NN);
+        m = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) {
+          const int sp = j / N, r = j % N;
+          diag[j] = G[sp * NN + (long long)r * N + r];
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (m > 0) {
+    flush(G, Ap, Bp, m, N, KK, NN);
+    __syncthreads();
+  }
+  if (f.g_in_smem)
+    for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) Gg[e] = Gs[e];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) fl[i] = sl[i];
+  if (threadIdx.x == 0) {
+    f.sign[c] = s_sign;
+    f.counts[3 * c + 0] += s_cnt[0];
+    f.counts[3 * c + 1] += s_cnt[1];
+    f.counts[3 * c + 2] += s_cnt[2];
+  }
+}
+
+}  // namespace
+
+size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem) {
+  size_t b = (size_t)(4 * kk * N + 2 * N) * elem;
+  if (g_in_smem) b += 2 * (size_t)N * N * elem;
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)N * sizeof(double) + (size_t)N + 16;
+  return b;
+}
+
+template <typename T>
+void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st) {
+  const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(T), f.g_in_smem);
+  cudaFuncSetAttribute(k_flip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  k_flip<T><<<n_chains, kThreads, bytes, st>>>(f);
+}
+
+template void flip_slice<double>(const FlipArgs<double>&, int, cudaStream_t);
+template void flip_slice<float>(const FlipArgs<float>&, int, cudaStream_t);
+
+}  // namespace nmc

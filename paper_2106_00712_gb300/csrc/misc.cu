@@ -1,0 +1,173 @@
+// Small device kernels: Philox field initialisation, conversions, and the equal-time
+// estimators.
+#include "nmc_internal.cuh"
+
+namespace nmc {
+
+namespace {
+
+__global__ void k_init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0, uint32_t k1,
+                              long long chain_offset) {
+  const long long total = (long long)n_chains * L * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / ((long long)L * N);
+    const uint32_t li = (uint32_t)(e - c * L * N);  // l*N + i
+    uint32_t ctr[4] = {li, 0u, (uint32_t)(chain_offset + c), kTagInit};
+    philox4x32_10(ctr, k0, k1);
+    s[e] = (ctr[0] >> 31) ? (int8_t)-1 : (int8_t)1;
+  }
+}
+
+__global__ void k_identity(double* U, double* D, double* T, int N, int batch) {
+  const long long NN = (long long)N * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NN * batch;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long rc = e % NN;
+    const double v = (rc / N == rc % N) ? 1.0 : 0.0;
+    if (U) U[e] = v;
+    if (T) T[e] = v;
+    if (D && rc < N) D[(e / NN) * N + rc] = 1.0;
+  }
+}
+
+__global__ void k_to_float(const double* x, float* y, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    y[e] = (float)x[e];
+}
+
+__global__ void k_to_double(const float* x, double* y, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    y[e] = (double)x[e];
+}
+
+__global__ void k_normalize(int8_t* s, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    s[e] = (s[e] == 1) ? (int8_t)1 : (int8_t)-1;
+}
+
+__global__ void k_philox(const uint32_t* c0, int n, uint32_t c1, uint32_t c2, uint32_t c3,
+                         uint32_t k0, uint32_t k1, uint32_t* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  uint32_t ctr[4] = {c0[j], c1, c2, c3};
+  philox4x32_10(ctr, k0, k1);
+  for (int w = 0; w < 4; ++w) out[4 * j + w] = ctr[w];
+}
+
+constexpr int kMeasThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kMeasThreads / 32; ++w) s += red[w];
+  return s;  // valid in thread 0
+}
+
+// Equal-time estimators on G~ (one CTA per chain), Eq. 3 energy and the S(Q) of Eq. 4:
+//  ekin  = -(1/N) sum_sigma sum_ij K_ij G~_ji
+//  epot  = (U/N) sum_i (1/2 - G~up_ii)(1/2 - G~dn_ii)
+//  docc  = (1/N) sum_i (1 - G~up_ii)(1 - G~dn_ii)
+//  dens  = (1/N) sum_i (2 - G~up_ii - G~dn_ii)
+//  S     = (1/4N) [ (sum_i p_i m_i)^2 + sum_sigma sum_ij p_i p_j (delta_ij - G~_ji) G~_ij ],
+//          m_i = G~dn_ii - G~up_ii, p_i = (-1)^{x_i + y_i}
+__global__ void __launch_bounds__(kMeasThreads)
+k_measure(const double* __restrict__ Gt, const double* __restrict__ K,
+          const double* __restrict__ sign, int Lx, int Ly, double U, double* __restrict__ acc) {
+  __shared__ double red[kMeasThreads / 32];
+  const int c = blockIdx.x;
+  const int N = Lx * Ly;
+  const long long NN = (long long)N * N;
+  const double* Gu = Gt + (long long)c * 2 * NN;
+  const double* Gd = Gu + NN;
+  double kin = 0.0, conn = 0.0;
+  for (long long e = threadIdx.x; e < NN; e += blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    const long long ji = (long long)j * N + i;
+    kin += K[e] * (Gu[ji] + Gd[ji]);
+    const double pij = (((i % Lx) + (i / Lx) + (j % Lx) + (j / Lx)) & 1) ? -1.0 : 1.0;
+    const double dij = (i == j) ? 1.0 : 0.0;
+    conn += pij * ((dij - Gu[ji]) * Gu[e] + (dij - Gd[ji]) * Gd[e]);
+  }
+  double epot = 0.0, docc = 0.0, dens = 0.0, stag = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double gu = Gu[(long long)i * N + i], gd = Gd[(long long)i * N + i];
+    epot += (0.5 - gu) * (0.5 - gd);
+    docc += (1.0 - gu) * (1.0 - gd);
+    dens += 2.0 - gu - gd;
+    const double p = (((i % Lx) + (i / Lx)) & 1) ? -1.0 : 1.0;
+    stag += p * (gd - gu);
+  }
+  kin = block_sum(kin, red);
+  conn = block_sum(conn, red);
+  epot = block_sum(epot, red);
+  docc = block_sum(docc, red);
+  dens = block_sum(dens, red);
+  stag = block_sum(stag, red);
+  if (threadIdx.x == 0) {
+    const double sg = sign[c];
+    const double ekin = -kin / N;
+    const double e = ekin + U * epot / N;
+    const double s = 0.25 * (stag * stag + conn) / N;
+    double* a = acc + (long long)c * 8;
+    a[0] += e * sg;
+    a[1] += ekin * sg;
+    a[2] += docc / N * sg;
+    a[3] += s * sg;
+    a[4] += dens / N * sg;
+    a[5] += sg;
+  }
+}
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+void init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0, uint32_t k1,
+                 long long chain_offset, cudaStream_t st) {
+  const long long n = (long long)n_chains * L * N;
+  k_init_fields<<<grid_for(n), 256, 0, st>>>(s, n_chains, L, N, k0, k1, chain_offset);
+}
+
+void set_identity_batch(double* U, double* D, double* T, int N, int batch, cudaStream_t st) {
+  k_identity<<<grid_for((long long)N * N * batch), 256, 0, st>>>(U, D, T, N, batch);
+}
+
+void copy_to_float(const double* x, float* y, long long n, cudaStream_t st) {
+  k_to_float<<<grid_for(n), 256, 0, st>>>(x, y, n);
+}
+
+void copy_to_double(const float* x, double* y, long long n, cudaStream_t st) {
+  k_to_double<<<grid_for(n), 256, 0, st>>>(x, y, n);
+}
+
+void fields_normalize(int8_t* s, long long n, cudaStream_t st) {
+  k_normalize<<<grid_for(n), 256, 0, st>>>(s, n);
+}
+
+void philox_batch(const uint32_t* c0, int n, uint32_t c1, uint32_t c2, uint32_t c3,
+                  uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st) {
+  if (n <= 0) return;
+  k_philox<<<(n + 255) / 256, 256, 0, st>>>(c0, n, c1, c2, c3, k0, k1, out);
+}
+
+void measure(const double* Gt, const double* K, const double* sign, int Lx, int Ly, double U,
+             double* acc, int n_chains, cudaStream_t st) {
+  k_measure<<<n_chains, kMeasThreads, 0, st>>>(Gt, K, sign, Lx, Ly, U, acc);
+}
+
+}  // namespace nmc

@@ -1,0 +1,905 @@
+// libnmc C ABI (include/nmc.h): context, device memory, and the sweep schedule.
+//
+// Schedule of one sweep over all chains (every step a batched kernel over chains x spins):
+//  up sweep (even phase), blocks j = 0..nb-1 of n_wrap slices:
+//    for l in block: flip slice l (k_flip), wrap G <- B_l G B_l^{-1}
+//    right stack R_{j+1} = B_block R_j (n_wrap GEMMs, column-pivoted QR, T <- T' T)
+//    recompute G = (I + R_{j+1} L_{j+1})^{-1} in FP64, record drift, replace G; measure
+//  down sweep (odd phase), blocks j = nb-1..0:
+//    for l in block, descending: wrap G <- B_l^{-1} G B_l, flip slice l
+//    left stack L_j = L_{j+1} B_block (held as L^T = U D T), recompute (I + R_j L_j)^{-1}
+// Stack slots 1..nb-1 hold R_j or L_j; slot 0 (R_0) and slot nb (L_nb) are the identity.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/nmc.h"
+#include "nmc_internal.cuh"
+
+namespace nmc_host {
+void hopping(int Lx, int Ly, double t, std::vector<double>& K);
+void jacobi_eigh(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V);
+void expk_from_eig(int n, const std::vector<double>& w, const std::vector<double>& V, double c,
+                   std::vector<double>& out);
+}  // namespace nmc_host
+
+namespace nmc {
+bool stab_needs_workspace(int N);
+}
+
+using namespace nmc;
+
+namespace {
+
+struct UDTBuf {
+  double* U = nullptr;
+  double* D = nullptr;
+  double* T = nullptr;
+};
+
+// A view of a batch of U D T factors (stride 0 = one shared matrix, e.g. the identity).
+struct UDTView {
+  const double* U;
+  long long sU;
+  const double* D;
+  long long sD;
+  const double* T;
+  long long sT;
+};
+
+constexpr uint64_t kCkptMagic = 0x4e4d43434b505431ull;  // "NMCCKPT1"
+
+}  // namespace
+
+struct nmc_ctx {
+  int Lx = 0, Ly = 0, N = 0, Lt = 0, w = 0, nb = 0;
+  double t = 0, U = 0, beta = 0, dtau = 0, lam = 0;
+  uint64_t seed = 0;
+  nmc_options opt{};
+  int kk = 16, g_in_smem = 0;
+  int device = -1;
+  bool configured = false, have_fields = false;
+  long long sweep_counter = 0;  // Philox counter word 1
+  long long phase = 0;          // sweeps since the fields were set (parity = direction)
+  std::string err;
+
+  std::vector<double> hK, hEm, hEp, hEmh, hEph;
+
+  // device memory
+  double *dK = nullptr, *dEm = nullptr, *dEp = nullptr, *dEmh = nullptr, *dEph = nullptr;
+  double *dI = nullptr, *dOnes = nullptr;
+  float *dEmf = nullptr, *dEpf = nullptr;
+  int8_t* dS = nullptr;
+  double *dG = nullptr, *dT1 = nullptr, *dX = nullptr, *dX2 = nullptr, *dTp = nullptr;
+  double *dM1 = nullptr, *dXs = nullptr, *dY = nullptr, *dWS = nullptr;
+  float *dGf = nullptr, *dT1f = nullptr;
+  std::vector<UDTBuf> slot;  // size nb + 1; entries 1..nb-1 allocated
+  UDTBuf spare;
+  double* dSign = nullptr;
+  unsigned long long* dCounts = nullptr;  // [chain][3]: attempts, accepts, disagreements
+  unsigned long long* dDrift = nullptr;   // [chain]: bits of max drift
+  double* dSeries = nullptr;              // [slot][chain][8]
+  long long series_cap = 0, n_series = 0;
+  uint8_t* dReplay = nullptr;
+  std::vector<void*> allocs;
+
+  cudaStream_t st() const { return (cudaStream_t)opt.cuda_stream; }
+  int chains() const { return opt.n_chains; }
+  int batch() const { return 2 * opt.n_chains; }
+  long long NN() const { return (long long)N * N; }
+  bool fp32() const { return opt.precision == NMC_FP32; }
+};
+
+namespace {
+
+nmc_status fail(nmc_ctx* x, nmc_status s, const std::string& msg) {
+  if (x) x->err = msg;
+  return s;
+}
+
+#define NMC_CUDA(x, call)                                                                   \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail((x), NMC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+#define NMC_TRY(expr)              \
+  do {                             \
+    nmc_status s_ = (expr);        \
+    if (s_ != NMC_OK) return s_;   \
+  } while (0)
+
+void free_all(nmc_ctx* x) {
+  for (void* p : x->allocs) cudaFree(p);
+  x->allocs.clear();
+  x->dK = x->dEm = x->dEp = x->dEmh = x->dEph = x->dI = x->dOnes = nullptr;
+  x->dEmf = x->dEpf = nullptr;
+  x->dS = nullptr;
+  x->dG = x->dT1 = x->dX = x->dX2 = x->dTp = x->dM1 = x->dXs = x->dY = x->dWS = nullptr;
+  x->dGf = x->dT1f = nullptr;
+  x->slot.clear();
+  x->spare = UDTBuf{};
+  x->dSign = nullptr;
+  x->dCounts = nullptr;
+  x->dDrift = nullptr;
+  x->dSeries = nullptr;
+  x->series_cap = x->n_series = 0;
+  x->dReplay = nullptr;
+  x->configured = false;
+  x->have_fields = false;
+}
+
+template <typename T>
+nmc_status dalloc(nmc_ctx* x, T** p, size_t count) {
+  void* q = nullptr;
+  const cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(x, NMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  x->allocs.push_back(q);
+  *p = (T*)q;
+  return NMC_OK;
+}
+
+nmc_status alloc_all(nmc_ctx* x) {
+  free_all(x);
+  NMC_CUDA(x, cudaGetDevice(&x->device));
+  const long long NN = x->NN();
+  const int B = x->batch();
+  const size_t mats = (size_t)B * NN;
+  NMC_TRY(dalloc(x, &x->dK, NN));
+  NMC_TRY(dalloc(x, &x->dEm, NN));
+  NMC_TRY(dalloc(x, &x->dEp, NN));
+  NMC_TRY(dalloc(x, &x->dEmh, NN));
+  NMC_TRY(dalloc(x, &x->dEph, NN));
+  NMC_TRY(dalloc(x, &x->dI, NN));
+  NMC_TRY(dalloc(x, &x->dOnes, x->N));
+  NMC_TRY(dalloc(x, &x->dS, (size_t)x->chains() * x->Lt * x->N));
+  NMC_TRY(dalloc(x, &x->dG, mats));
+  NMC_TRY(dalloc(x, &x->dT1, mats));
+  NMC_TRY(dalloc(x, &x->dX, mats));
+  NMC_TRY(dalloc(x, &x->dX2, mats));
+  NMC_TRY(dalloc(x, &x->dTp, mats));
+  NMC_TRY(dalloc(x, &x->dM1, mats));
+  NMC_TRY(dalloc(x, &x->dXs, mats));
+  NMC_TRY(dalloc(x, &x->dY, mats));
+  if (stab_needs_workspace(x->N)) NMC_TRY(dalloc(x, &x->dWS, 2 * mats));
+  if (x->fp32()) {
+    NMC_TRY(dalloc(x, &x->dEmf, NN));
+    NMC_TRY(dalloc(x, &x->dEpf, NN));
+    NMC_TRY(dalloc(x, &x->dGf, mats));
+    NMC_TRY(dalloc(x, &x->dT1f, mats));
+  }
+  x->slot.assign(x->nb + 1, UDTBuf{});
+  auto alloc_udt = [&](UDTBuf& u) -> nmc_status {
+    NMC_TRY(dalloc(x, &u.U, mats));
+    NMC_TRY(dalloc(x, &u.D, (size_t)B * x->N));
+    NMC_TRY(dalloc(x, &u.T, mats));
+    return NMC_OK;
+  };
+  for (int j = 1; j < x->nb; ++j) NMC_TRY(alloc_udt(x->slot[j]));
+  NMC_TRY(alloc_udt(x->spare));
+  NMC_TRY(dalloc(x, &x->dSign, x->chains()));
+  NMC_TRY(dalloc(x, &x->dCounts, 3 * (size_t)x->chains()));
+  NMC_TRY(dalloc(x, &x->dDrift, x->chains()));
+
+  cudaStream_t st = x->st();
+  const size_t mb = NN * sizeof(double);
+  NMC_CUDA(x, cudaMemcpyAsync(x->dK, x->hK.data(), mb, cudaMemcpyHostToDevice, st));
+  NMC_CUDA(x, cudaMemcpyAsync(x->dEm, x->hEm.data(), mb, cudaMemcpyHostToDevice, st));
+  NMC_CUDA(x, cudaMemcpyAsync(x->dEp, x->hEp.data(), mb, cudaMemcpyHostToDevice, st));
+  NMC_CUDA(x, cudaMemcpyAsync(x->dEmh, x->hEmh.data(), mb, cudaMemcpyHostToDevice, st));
+  NMC_CUDA(x, cudaMemcpyAsync(x->dEph, x->hEph.data(), mb, cudaMemcpyHostToDevice, st));
+  set_identity_batch(x->dI, x->dOnes, nullptr, x->N, 1, st);
+  if (x->fp32()) {
+    copy_to_float(x->dEm, x->dEmf, NN, st);
+    copy_to_float(x->dEp, x->dEpf, NN, st);
+  }
+  NMC_CUDA(x, cudaGetLastError());
+  NMC_CUDA(x, cudaStreamSynchronize(st));
+  x->configured = true;
+  return NMC_OK;
+}
+
+nmc_status ensure_configured(nmc_ctx* x) {
+  if (x->configured) {
+    NMC_CUDA(x, cudaSetDevice(x->device));
+    return NMC_OK;
+  }
+  return alloc_all(x);
+}
+
+void clamp_delay(nmc_ctx* x) {
+  const size_t elem = x->fp32() ? sizeof(float) : sizeof(double);
+  const size_t limit = 200 * 1024;
+  int kk = std::max(1, std::min(x->opt.delay_k, x->N));
+  x->g_in_smem = flip_smem_bytes(x->N, kk, elem, 1) <= limit ? 1 : 0;
+  while (kk > 1 && flip_smem_bytes(x->N, kk, elem, x->g_in_smem) > limit) --kk;
+  x->kk = kk;
+}
+
+// ---------------------------------------------------------------------------- GEMM helpers
+ScaleDesc field_scale(const nmc_ctx* x, int l, bool inv) {
+  ScaleDesc d;
+  d.kind = inv ? SC_FIELD_INV : SC_FIELD;
+  d.fields = x->dS + (long long)l * x->N;
+  d.fstride = (long long)x->Lt * x->N;
+  d.e_lam = std::exp(x->lam);
+  d.e_mlam = std::exp(-x->lam);
+  return d;
+}
+
+ScaleDesc vec_scale(const double* v, long long stride, int kind) {
+  ScaleDesc d;
+  d.kind = kind;
+  d.vec = v;
+  d.vstride = stride;
+  return d;
+}
+
+template <typename T>
+GemmArgs<T> gemm_base(const nmc_ctx* x, const T* A, long long sA, const T* B, long long sB,
+                      T* C) {
+  GemmArgs<T> g;
+  g.M = g.N = g.K = x->N;
+  g.batch = x->batch();
+  g.A = A; g.sA = sA; g.lda = x->N;
+  g.B = B; g.sB = sB; g.ldb = x->N;
+  g.C = C; g.sC = x->NN(); g.ldc = x->N;
+  return g;
+}
+
+UDTView identity_view(const nmc_ctx* x) { return UDTView{x->dI, 0, x->dOnes, 0, x->dI, 0}; }
+UDTView view_of(const nmc_ctx* x, const UDTBuf& b) {
+  return UDTView{b.U, x->NN(), b.D, x->N, b.T, x->NN()};
+}
+
+// ---------------------------------------------------------------------------- steps
+void wrap(nmc_ctx* x, int l, bool up) {
+  cudaStream_t st = x->st();
+  const long long NN = x->NN();
+  if (x->fp32()) {
+    if (up) {  // T1 = Em (e^V G e^-V); G = T1 Ep
+      auto g = gemm_base<float>(x, x->dEmf, 0, x->dGf, NN, x->dT1f);
+      g.brow = field_scale(x, l, false);
+      g.bcol = field_scale(x, l, true);
+      gemm(g, st);
+      gemm(gemm_base<float>(x, x->dT1f, NN, x->dEpf, 0, x->dGf), st);
+    } else {   // T1 = Ep G; G = e^-V (T1 Em) e^V
+      gemm(gemm_base<float>(x, x->dEpf, 0, x->dGf, NN, x->dT1f), st);
+      auto g = gemm_base<float>(x, x->dT1f, NN, x->dEmf, 0, x->dGf);
+      g.crow = field_scale(x, l, true);
+      g.ccol = field_scale(x, l, false);
+      gemm(g, st);
+    }
+  } else {
+    if (up) {
+      auto g = gemm_base<double>(x, x->dEm, 0, x->dG, NN, x->dT1);
+      g.brow = field_scale(x, l, false);
+      g.bcol = field_scale(x, l, true);
+      gemm(g, st);
+      gemm(gemm_base<double>(x, x->dT1, NN, x->dEp, 0, x->dG), st);
+    } else {
+      gemm(gemm_base<double>(x, x->dEp, 0, x->dG, NN, x->dT1), st);
+      auto g = gemm_base<double>(x, x->dT1, NN, x->dEm, 0, x->dG);
+      g.crow = field_scale(x, l, true);
+      g.ccol = field_scale(x, l, false);
+      gemm(g, st);
+    }
+  }
+}
+
+void flip(nmc_ctx* x, int l, const uint8_t* replay) {
+  const uint32_t k0 = (uint32_t)(x->seed & 0xffffffffu), k1 = (uint32_t)(x->seed >> 32);
+  const double dm = std::exp(-2.0 * x->lam) - 1.0, dp = std::exp(2.0 * x->lam) - 1.0;
+  if (x->fp32()) {
+    FlipArgs<float> f{x->dGf, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
+                      (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
+                      x->dCounts, replay, nullptr};
+    flip_slice(f, x->chains(), x->st());
+  } else {
+    FlipArgs<double> f{x->dG, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
+                       (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
+                       x->dCounts, replay, nullptr};
+    flip_slice(f, x->chains(), x->st());
+  }
+}
+
+// dst = QRP-UDT of (product of block j's B matrices) applied to src; right: B_block src,
+// left (transposed stack): B_block^T src.
+void stack_update(nmc_ctx* x, int j, const UDTView& src, const UDTBuf& dst, bool right) {
+  cudaStream_t st = x->st();
+  const long long NN = x->NN();
+  const int w = x->w;
+  double* X = x->dX;
+  double* X2 = x->dX2;
+  if (right) {
+    const int l0 = j * w;
+    auto g = gemm_base<double>(x, x->dEm, 0, src.U, src.sU, X);
+    g.brow = field_scale(x, l0, false);
+    g.bcol = vec_scale(src.D, src.sD, SC_VEC);
+    gemm(g, st);
+    for (int l = l0 + 1; l < l0 + w; ++l) {
+      auto h = gemm_base<double>(x, x->dEm, 0, X, NN, X2);
+      h.brow = field_scale(x, l, false);
+      gemm(h, st);
+      std::swap(X, X2);
+    }
+  } else {
+    const int lt = (j + 1) * w - 1;
+    auto g = gemm_base<double>(x, x->dEm, 0, src.U, src.sU, X);
+    g.bcol = vec_scale(src.D, src.sD, SC_VEC);
+    g.crow = field_scale(x, lt, false);
+    gemm(g, st);
+    for (int l = lt - 1; l >= j * w; --l) {
+      auto h = gemm_base<double>(x, x->dEm, 0, X, NN, X2);
+      h.crow = field_scale(x, l, false);
+      gemm(h, st);
+      std::swap(X, X2);
+    }
+  }
+  qrp_udt(X, dst.U, dst.D, x->dTp, x->dWS, x->N, x->batch(), st);
+  gemm(gemm_base<double>(x, x->dTp, NN, src.T, src.sT, dst.T), st);
+}
+
+// G = (I + R L)^{-1} with R = U_R D_R T_R, L^T = U_L D_L T_L:
+//   X = Db_R^{-1} (U_R^T U_L) Db_L^{-1} + Ds_R (T_R T_L^T) Ds_L
+//   G = U_L Db_L^{-1} X^{-1} Db_R^{-1} U_R^T
+void recompute(nmc_ctx* x, const UDTView& R, const UDTView& L, bool drift) {
+  cudaStream_t st = x->st();
+  const long long NN = x->NN();
+  auto g1 = gemm_base<double>(x, R.U, R.sU, L.U, L.sU, x->dM1);
+  g1.transA = 1;
+  g1.crow = vec_scale(R.D, R.sD, SC_INV_MAX1);
+  g1.ccol = vec_scale(L.D, L.sD, SC_INV_MAX1);
+  gemm(g1, st);
+  auto g2 = gemm_base<double>(x, R.T, R.sT, L.T, L.sT, x->dXs);
+  g2.transB = 1;
+  g2.crow = vec_scale(R.D, R.sD, SC_MIN1);
+  g2.ccol = vec_scale(L.D, L.sD, SC_MIN1);
+  g2.Cin = x->dM1; g2.sCin = NN; g2.ldcin = x->N; g2.beta = 1.0;
+  gemm(g2, st);
+  solve_stab(x->dXs, R.U, R.sU, R.D, R.sD, x->dY, x->dWS, x->N, x->batch(), st);
+  auto g3 = gemm_base<double>(x, L.U, L.sU, x->dY, NN, x->dG);
+  g3.brow = vec_scale(L.D, L.sD, SC_INV_MAX1);
+  if (drift) {
+    g3.ref = x->fp32() ? (const void*)x->dGf : (const void*)x->dG;
+    g3.ref_is_float = x->fp32() ? 1 : 0;
+    g3.sRef = NN;
+    g3.drift = x->dDrift;
+  }
+  if (x->fp32()) { g3.Cf = x->dGf; g3.sCf = NN; }
+  gemm(g3, st);
+}
+
+void measure_now(nmc_ctx* x) {
+  cudaStream_t st = x->st();
+  const long long NN = x->NN();
+  gemm(gemm_base<double>(x, x->dEph, 0, x->dG, NN, x->dT1), st);   // e^{dtau K/2} G
+  gemm(gemm_base<double>(x, x->dT1, NN, x->dEmh, 0, x->dM1), st);  // ... e^{-dtau K/2}
+  double* acc = x->dSeries + x->n_series * (long long)x->chains() * 8;
+  nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), st);
+}
+
+void sweep_up(nmc_ctx* x, bool meas, const uint8_t* replay) {
+  const int nb = x->nb, w = x->w;
+  for (int j = 0; j < nb; ++j) {
+    for (int l = j * w; l < (j + 1) * w; ++l) {
+      flip(x, l, replay);
+      wrap(x, l, true);
+    }
+    const UDTView src = (j == 0) ? identity_view(x) : view_of(x, x->slot[j]);
+    stack_update(x, j, src, x->spare, true);
+    const UDTView Lv = (j + 1 == nb) ? identity_view(x) : view_of(x, x->slot[j + 1]);
+    recompute(x, view_of(x, x->spare), Lv, true);
+    if (j + 1 < nb) std::swap(x->spare, x->slot[j + 1]);
+    if (meas) measure_now(x);
+  }
+}
+
+void sweep_down(nmc_ctx* x, bool meas, const uint8_t* replay) {
+  const int nb = x->nb, w = x->w;
+  for (int j = nb - 1; j >= 0; --j) {
+    for (int l = (j + 1) * w - 1; l >= j * w; --l) {
+      wrap(x, l, false);
+      flip(x, l, replay);
+    }
+    const UDTView src = (j + 1 == nb) ? identity_view(x) : view_of(x, x->slot[j + 1]);
+    stack_update(x, j, src, x->spare, false);
+    const UDTView Rv = (j == 0) ? identity_view(x) : view_of(x, x->slot[j]);
+    recompute(x, Rv, view_of(x, x->spare), true);
+    if (j >= 1) std::swap(x->spare, x->slot[j]);
+    if (meas) measure_now(x);
+  }
+}
+
+// Build the stacks a sweep of the given direction needs, and G, from the fields alone.
+void build_stacks(nmc_ctx* x, bool for_up) {
+  const int nb = x->nb;
+  if (for_up) {  // left stacks L_j, j = nb-1..1; G_0 = (I + L_0)^{-1}
+    for (int j = nb - 1; j >= 0; --j) {
+      const UDTView src = (j + 1 == nb) ? identity_view(x) : view_of(x, x->slot[j + 1]);
+      stack_update(x, j, src, x->spare, false);
+      if (j >= 1) std::swap(x->spare, x->slot[j]);
+    }
+    recompute(x, identity_view(x), view_of(x, x->spare), false);
+  } else {       // right stacks R_j, j = 1..nb-1; G_L = (I + R_nb)^{-1}
+    for (int j = 0; j < nb; ++j) {
+      const UDTView src = (j == 0) ? identity_view(x) : view_of(x, x->slot[j]);
+      stack_update(x, j, src, x->spare, true);
+      if (j + 1 < nb) std::swap(x->spare, x->slot[j + 1]);
+    }
+    recompute(x, view_of(x, x->spare), identity_view(x), false);
+  }
+}
+
+nmc_status reset_chain_state(nmc_ctx* x) {
+  cudaStream_t st = x->st();
+  std::vector<double> ones(x->chains(), 1.0);
+  NMC_CUDA(x, cudaMemcpyAsync(x->dSign, ones.data(), ones.size() * sizeof(double),
+                              cudaMemcpyHostToDevice, st));
+  NMC_CUDA(x, cudaMemsetAsync(x->dCounts, 0, 3 * sizeof(unsigned long long) * x->chains(), st));
+  NMC_CUDA(x, cudaMemsetAsync(x->dDrift, 0, sizeof(unsigned long long) * x->chains(), st));
+  x->n_series = 0;
+  x->phase = 0;
+  NMC_CUDA(x, cudaStreamSynchronize(st));
+  return NMC_OK;
+}
+
+nmc_status after_fields(nmc_ctx* x) {
+  NMC_TRY(reset_chain_state(x));
+  build_stacks(x, true);
+  NMC_CUDA(x, cudaGetLastError());
+  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  x->have_fields = true;
+  return NMC_OK;
+}
+
+nmc_status ensure_series(nmc_ctx* x, long long need) {
+  if (need <= x->series_cap) return NMC_OK;
+  long long cap = std::max<long long>(need, 2 * x->series_cap);
+  cap = std::max<long long>(cap, 16);
+  double* p = nullptr;
+  const size_t bytes = (size_t)cap * x->chains() * 8 * sizeof(double);
+  const cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(x, NMC_ENOMEM, "series buffer: cudaMalloc failed");
+  }
+  NMC_CUDA(x, cudaMemsetAsync(p, 0, bytes, x->st()));
+  if (x->dSeries && x->n_series > 0)
+    NMC_CUDA(x, cudaMemcpyAsync(p, x->dSeries, (size_t)x->n_series * x->chains() * 8 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, x->st()));
+  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  if (x->dSeries) {
+    x->allocs.erase(std::remove(x->allocs.begin(), x->allocs.end(), (void*)x->dSeries),
+                    x->allocs.end());
+    cudaFree(x->dSeries);
+  }
+  x->dSeries = p;
+  x->allocs.push_back(p);
+  x->series_cap = cap;
+  return NMC_OK;
+}
+
+nmc_status check_drift(nmc_ctx* x) {
+  std::vector<unsigned long long> bits(x->chains());
+  NMC_CUDA(x, cudaMemcpyAsync(bits.data(), x->dDrift, bits.size() * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, x->st()));
+  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  double tol = x->opt.drift_tol;
+  if (tol <= 0) tol = x->fp32() ? 1e-3 : 1e-6;
+  for (size_t c = 0; c < bits.size(); ++c) {
+    double d;
+    std::memcpy(&d, &bits[c], sizeof d);
+    if (!std::isfinite(d) || d > tol) {
+      char buf[160];
+      std::snprintf(buf, sizeof buf, "chain %zu: stabilization drift %.3e exceeds %.1e", c, d, tol);
+      return fail(x, NMC_ENUMERIC, buf);
+    }
+  }
+  return NMC_OK;
+}
+
+nmc_status run_sweeps(nmc_ctx* x, int n, int meas, const uint8_t* replay) {
+  if (meas) NMC_TRY(ensure_series(x, x->n_series + n));
+  for (int s = 0; s < n; ++s) {
+    if (x->phase % 2 == 0) sweep_up(x, meas != 0, replay);
+    else sweep_down(x, meas != 0, replay);
+    NMC_CUDA(x, cudaGetLastError());
+    ++x->phase;
+    ++x->sweep_counter;
+    if (meas) ++x->n_series;
+  }
+  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  return check_drift(x);
+}
+
+bool valid_fields(const int8_t* s, size_t n) {
+  for (size_t e = 0; e < n; ++e)
+    if (s[e] != 1 && s[e] != -1) return false;
+  return true;
+}
+
+void binned(const std::vector<double>& series, int nbins, double& mean, double& err) {
+  const size_t n = series.size();
+  mean = 0;
+  err = 0;
+  if (n == 0) return;
+  for (double v : series) mean += v;
+  mean /= n;
+  if ((int)n < nbins || nbins < 2) return;
+  const size_t per = n / nbins;
+  std::vector<double> b(nbins, 0.0);
+  for (int k = 0; k < nbins; ++k) {
+    for (size_t e = 0; e < per; ++e) b[k] += series[k * per + e];
+    b[k] /= per;
+  }
+  double m = 0;
+  for (double v : b) m += v;
+  m /= nbins;
+  double var = 0;
+  for (double v : b) var += (v - m) * (v - m);
+  err = std::sqrt(var / (nbins - 1) / nbins);
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+void nmc_default_options(nmc_options* o) {
+  if (!o) return;
+  o->n_chains = 1;
+  o->delay_k = 16;
+  o->precision = NMC_FP64;
+  o->drift_tol = 0.0;
+  o->chain_offset = 0;
+  o->cuda_stream = nullptr;
+}
+
+nmc_status nmc_create(int Lx, int Ly, double t, double U, double beta, double dtau, int n_wrap,
+                      uint64_t seed, nmc_ctx** out) {
+  if (!out) return NMC_EINVAL;
+  *out = nullptr;
+  if (Lx < 1 || Ly < 1 || Lx * Ly < 2 || Lx * Ly > 1024) return NMC_EINVAL;
+  if ((Lx > 1 && Lx % 2) || (Ly > 1 && Ly % 2)) return NMC_EINVAL;
+  if (!(t > 0) || !(U >= 0) || !(beta > 0) || !(dtau > 0) || n_wrap < 1) return NMC_EINVAL;
+  const double ratio = beta / dtau;
+  const double Ltd = std::round(ratio);
+  if (Ltd < 1 || std::fabs(ratio - Ltd) > 1e-9 * ratio || Ltd > 1e6) return NMC_EINVAL;
+  const int Lt = (int)Ltd;
+  if (Lt % n_wrap) return NMC_EINVAL;
+  nmc_ctx* x = new (std::nothrow) nmc_ctx();
+  if (!x) return NMC_ENOMEM;
+  x->Lx = Lx; x->Ly = Ly; x->N = Lx * Ly; x->Lt = Lt; x->w = n_wrap; x->nb = Lt / n_wrap;
+  x->t = t; x->U = U; x->beta = beta; x->dtau = dtau; x->seed = seed;
+  x->lam = std::acosh(std::exp(dtau * U / 2.0));
+  nmc_default_options(&x->opt);
+  nmc_host::hopping(Lx, Ly, t, x->hK);
+  std::vector<double> A = x->hK, wv, V;
+  nmc_host::jacobi_eigh(x->N, A, wv, V);
+  nmc_host::expk_from_eig(x->N, wv, V, -dtau, x->hEm);
+  nmc_host::expk_from_eig(x->N, wv, V, +dtau, x->hEp);
+  nmc_host::expk_from_eig(x->N, wv, V, -dtau / 2, x->hEmh);
+  nmc_host::expk_from_eig(x->N, wv, V, +dtau / 2, x->hEph);
+  clamp_delay(x);
+  *out = x;
+  return NMC_OK;
+}
+
+nmc_status nmc_configure(nmc_ctx* x, const nmc_options* o) {
+  if (!x) return NMC_EINVAL;
+  if (x->have_fields) return fail(x, NMC_ESTATE, "nmc_configure after fields were set");
+  nmc_options n;
+  nmc_default_options(&n);
+  if (o) n = *o;
+  if (n.n_chains < 1 || n.delay_k < 1 || (n.precision != NMC_FP64 && n.precision != NMC_FP32) ||
+      n.chain_offset < 0 || n.n_chains > (1 << 20))
+    return fail(x, NMC_EINVAL, "invalid nmc_options");
+  x->opt = n;
+  clamp_delay(x);
+  return alloc_all(x);
+}
+
+nmc_status nmc_set_fields(nmc_ctx* x, const int8_t* s, size_t n) {
+  if (!x || !s) return NMC_EINVAL;
+  const size_t need = (size_t)x->opt.n_chains * x->Lt * x->N;
+  if (n != need) return fail(x, NMC_EINVAL, "nmc_set_fields: size mismatch");
+  if (!valid_fields(s, n)) return fail(x, NMC_EINVAL, "nmc_set_fields: values must be +1 or -1");
+  NMC_TRY(ensure_configured(x));
+  NMC_CUDA(x, cudaMemcpyAsync(x->dS, s, n, cudaMemcpyHostToDevice, x->st()));
+  return after_fields(x);
+}
+
+nmc_status nmc_set_fields_device(nmc_ctx* x, const int8_t* d_s, size_t n) {
+  if (!x || !d_s) return NMC_EINVAL;
+  const size_t need = (size_t)x->opt.n_chains * x->Lt * x->N;
+  if (n != need) return fail(x, NMC_EINVAL, "nmc_set_fields_device: size mismatch");
+  NMC_TRY(ensure_configured(x));
+  NMC_CUDA(x, cudaMemcpyAsync(x->dS, d_s, n, cudaMemcpyDeviceToDevice, x->st()));
+  fields_normalize(x->dS, (long long)n, x->st());
+  return after_fields(x);
+}
+
+nmc_status nmc_generate(nmc_ctx* x, int mode, const void* model) {
+  (void)model;
+  if (!x) return NMC_EINVAL;
+  if (mode != 0) return fail(x, NMC_EINVAL, "nmc_generate: only mode 0 (random) is available");
+  NMC_TRY(ensure_configured(x));
+  init_fields(x->dS, x->chains(), x->Lt, x->N, (uint32_t)(x->seed & 0xffffffffu),
+              (uint32_t)(x->seed >> 32), x->opt.chain_offset, x->st());
+  NMC_CUDA(x, cudaGetLastError());
+  return after_fields(x);
+}
+
+nmc_status nmc_sweep(nmc_ctx* x, int n_sweeps, int measure) {
+  if (!x || n_sweeps < 0) return NMC_EINVAL;
+  if (!x->have_fields) return fail(x, NMC_ESTATE, "nmc_sweep before fields were set");
+  NMC_TRY(ensure_configured(x));
+  return run_sweeps(x, n_sweeps, measure, nullptr);
+}
+
+nmc_status nmc_sweep_replay(nmc_ctx* x, const uint8_t* accept, size_t n, int measure) {
+  if (!x || !accept) return NMC_EINVAL;
+  if (!x->have_fields) return fail(x, NMC_ESTATE, "nmc_sweep_replay before fields were set");
+  const size_t need = (size_t)x->opt.n_chains * x->Lt * x->N;
+  if (n != need) return fail(x, NMC_EINVAL, "nmc_sweep_replay: size mismatch");
+  NMC_TRY(ensure_configured(x));
+  if (!x->dReplay) NMC_TRY(dalloc(x, &x->dReplay, need));
+  NMC_CUDA(x, cudaMemcpyAsync(x->dReplay, accept, n, cudaMemcpyHostToDevice, x->st()));
+  return run_sweeps(x, 1, measure, x->dReplay);
+}
+
+nmc_status nmc_measure(nmc_ctx* x, nmc_obs* per_chain, nmc_obs* pooled) {
+  if (!x) return NMC_EINVAL;
+  if (!x->configured) return fail(x, NMC_ESTATE, "nmc_measure before configuration");
+  NMC_CUDA(x, cudaSetDevice(x->device));
+  const int C = x->chains();
+  const long long S = x->n_series;
+  std::vector<double> ser((size_t)S * C * 8);
+  std::vector<unsigned long long> cnt(3 * (size_t)C), dr(C);
+  cudaStream_t st = x->st();
+  if (S > 0)
+    NMC_CUDA(x, cudaMemcpyAsync(ser.data(), x->dSeries, ser.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+  NMC_CUDA(x, cudaMemcpyAsync(cnt.data(), x->dCounts, cnt.size() * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, st));
+  NMC_CUDA(x, cudaMemcpyAsync(dr.data(), x->dDrift, dr.size() * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, st));
+  NMC_CUDA(x, cudaStreamSynchronize(st));
+  const long long per_sweep = x->nb;
+  std::vector<nmc_obs> pc(C);
+  // per chain
+  for (int c = 0; c < C; ++c) {
+    nmc_obs& o = pc[c];
+    std::memset(&o, 0, sizeof o);
+    nmc_est* est[6] = {&o.energy, &o.ekin, &o.double_occ, &o.s_pipi, &o.density, &o.sign};
+    double tot[6] = {0, 0, 0, 0, 0, 0};
+    for (long long s = 0; s < S; ++s)
+      for (int k = 0; k < 6; ++k) tot[k] += ser[((size_t)s * C + c) * 8 + k];
+    for (int k = 0; k < 5; ++k) {
+      std::vector<double> seq;
+      for (long long s = 0; s < S; ++s) {
+        const double* a = &ser[((size_t)s * C + c) * 8];
+        seq.push_back(a[5] != 0 ? a[k] / a[5] : 0.0);
+      }
+      double m, e;
+      binned(seq, 10, m, e);
+      est[k]->mean = tot[5] != 0 ? tot[k] / tot[5] : 0.0;
+      est[k]->err = e;
+    }
+    {
+      std::vector<double> seq;
+      for (long long s = 0; s < S; ++s) seq.push_back(ser[((size_t)s * C + c) * 8 + 5] / per_sweep);
+      double m, e;
+      binned(seq, 10, m, e);
+      o.sign.mean = S > 0 ? tot[5] / (S * per_sweep) : 0.0;
+      o.sign.err = e;
+    }
+    o.accept = cnt[3 * c] ? (double)cnt[3 * c + 1] / (double)cnt[3 * c] : 0.0;
+    std::memcpy(&o.max_drift, &dr[c], sizeof(double));
+    o.n_meas = S * per_sweep;
+    o.n_disagree = (long long)cnt[3 * c + 2];
+  }
+  if (per_chain) std::memcpy(per_chain, pc.data(), C * sizeof(nmc_obs));
+  if (pooled) {
+    nmc_obs p;
+    std::memset(&p, 0, sizeof p);
+    auto pool = [&](nmc_est nmc_obs::*fld, nmc_est& dst) {
+      double m = 0;
+      for (int c = 0; c < C; ++c) m += (pc[c].*fld).mean;
+      m /= C;
+      double e = 0;
+      if (C >= 2) {
+        double v = 0;
+        for (int c = 0; c < C; ++c) v += ((pc[c].*fld).mean - m) * ((pc[c].*fld).mean - m);
+        e = std::sqrt(v / (C - 1) / C);
+      } else {
+        e = (pc[0].*fld).err;
+      }
+      dst.mean = m;
+      dst.err = e;
+    };
+    pool(&nmc_obs::energy, p.energy);
+    pool(&nmc_obs::ekin, p.ekin);
+    pool(&nmc_obs::double_occ, p.double_occ);
+    pool(&nmc_obs::s_pipi, p.s_pipi);
+    pool(&nmc_obs::density, p.density);
+    pool(&nmc_obs::sign, p.sign);
+    unsigned long long att = 0, acc = 0, dis = 0;
+    for (int c = 0; c < C; ++c) {
+      att += cnt[3 * c];
+      acc += cnt[3 * c + 1];
+      dis += cnt[3 * c + 2];
+      p.max_drift = std::max(p.max_drift, pc[c].max_drift);
+    }
+    p.accept = att ? (double)acc / (double)att : 0.0;
+    p.n_meas = S * per_sweep;
+    p.n_disagree = (long long)dis;
+    *pooled = p;
+  }
+  return NMC_OK;
+}
+
+nmc_status nmc_get_fields(nmc_ctx* x, int8_t* s, size_t n) {
+  if (!x || !s) return NMC_EINVAL;
+  if (!x->have_fields) return fail(x, NMC_ESTATE, "no fields set");
+  const size_t need = (size_t)x->opt.n_chains * x->Lt * x->N;
+  if (n != need) return fail(x, NMC_EINVAL, "nmc_get_fields: size mismatch");
+  NMC_CUDA(x, cudaSetDevice(x->device));
+  NMC_CUDA(x, cudaMemcpyAsync(s, x->dS, n, cudaMemcpyDeviceToHost, x->st()));
+  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  return NMC_OK;
+}
+
+nmc_status nmc_get_green(nmc_ctx* x, int chain, int spin, double* G) {
+  if (!x || !G || chain < 0 || chain >= x->opt.n_chains || spin < 0 || spin > 1)
+    return NMC_EINVAL;
+  if (!x->have_fields) return fail(x, NMC_ESTATE, "no fields set");
+  NMC_CUDA(x, cudaSetDevice(x->device));
+  const long long NN = x->NN();
+  const long long off = ((long long)chain * 2 + spin) * NN;
+  if (x->fp32()) {
+    std::vector<float> tmp(NN);
+    NMC_CUDA(x, cudaMemcpyAsync(tmp.data(), x->dGf + off, NN * sizeof(float),
+                                cudaMemcpyDeviceToHost, x->st()));
+    NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+    for (long long e = 0; e < NN; ++e) G[e] = tmp[e];
+  } else {
+    NMC_CUDA(x, cudaMemcpyAsync(G, x->dG + off, NN * sizeof(double), cudaMemcpyDeviceToHost,
+                                x->st()));
+    NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  }
+  return NMC_OK;
+}
+
+nmc_status nmc_get_dims(const nmc_ctx* x, int* N, int* L_tau, int* n_chains, int* delay_k) {
+  if (!x) return NMC_EINVAL;
+  if (N) *N = x->N;
+  if (L_tau) *L_tau = x->Lt;
+  if (n_chains) *n_chains = x->opt.n_chains;
+  if (delay_k) *delay_k = x->kk;
+  return NMC_OK;
+}
+
+// checkpoint layout: u64 magic, i64 N, Lt, chains, seed, sweep_counter, phase, n_series,
+// precision; then fields (int8), sign (f64), counts (u64 x3), drift (u64), series (f64)
+nmc_status nmc_checkpoint(nmc_ctx* x, void* buf, size_t* n) {
+  if (!x || !n) return NMC_EINVAL;
+  if (!x->have_fields) return fail(x, NMC_ESTATE, "no fields set");
+  const int C = x->chains();
+  const size_t nf = (size_t)C * x->Lt * x->N;
+  const size_t nser = (size_t)x->n_series * C * 8;
+  const size_t hdr = 9 * sizeof(int64_t);
+  const size_t total = hdr + nf + C * sizeof(double) + 3 * C * sizeof(uint64_t) +
+                       C * sizeof(uint64_t) + nser * sizeof(double);
+  if (!buf) { *n = total; return NMC_OK; }
+  if (*n < total) return fail(x, NMC_EINVAL, "nmc_checkpoint: buffer too small");
+  NMC_CUDA(x, cudaSetDevice(x->device));
+  char* p = (char*)buf;
+  const int64_t h[9] = {(int64_t)kCkptMagic, x->N, x->Lt, C, (int64_t)x->seed, x->sweep_counter,
+                        x->phase, x->n_series, x->opt.precision};
+  std::memcpy(p, h, hdr);
+  p += hdr;
+  cudaStream_t st = x->st();
+  NMC_CUDA(x, cudaMemcpyAsync(p, x->dS, nf, cudaMemcpyDeviceToHost, st)); p += nf;
+  NMC_CUDA(x, cudaMemcpyAsync(p, x->dSign, C * sizeof(double), cudaMemcpyDeviceToHost, st));
+  p += C * sizeof(double);
+  NMC_CUDA(x, cudaMemcpyAsync(p, x->dCounts, 3 * C * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  p += 3 * C * sizeof(uint64_t);
+  NMC_CUDA(x, cudaMemcpyAsync(p, x->dDrift, C * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  p += C * sizeof(uint64_t);
+  if (nser)
+    NMC_CUDA(x, cudaMemcpyAsync(p, x->dSeries, nser * sizeof(double), cudaMemcpyDeviceToHost, st));
+  NMC_CUDA(x, cudaStreamSynchronize(st));
+  *n = total;
+  return NMC_OK;
+}
+
+nmc_status nmc_restore(nmc_ctx* x, const void* buf, size_t n) {
+  if (!x || !buf) return NMC_EINVAL;
+  const size_t hdr = 9 * sizeof(int64_t);
+  if (n < hdr) return fail(x, NMC_EINVAL, "nmc_restore: truncated");
+  int64_t h[9];
+  std::memcpy(h, buf, hdr);
+  const int C = x->opt.n_chains;
+  if ((uint64_t)h[0] != kCkptMagic || h[1] != x->N || h[2] != x->Lt || h[3] != C ||
+      (uint64_t)h[4] != x->seed || h[8] != x->opt.precision)
+    return fail(x, NMC_EINVAL, "nmc_restore: checkpoint does not match this context");
+  const size_t nf = (size_t)C * x->Lt * x->N;
+  const long long ns = h[7];
+  const size_t nser = (size_t)ns * C * 8;
+  const size_t total = hdr + nf + C * sizeof(double) + 4 * C * sizeof(uint64_t) + nser * sizeof(double);
+  if (n < total) return fail(x, NMC_EINVAL, "nmc_restore: truncated");
+  const char* p = (const char*)buf + hdr;
+  if (!valid_fields((const int8_t*)p, nf)) return fail(x, NMC_EINVAL, "nmc_restore: bad fields");
+  NMC_TRY(ensure_configured(x));
+  cudaStream_t st = x->st();
+  NMC_CUDA(x, cudaMemcpyAsync(x->dS, p, nf, cudaMemcpyHostToDevice, st)); p += nf;
+  NMC_CUDA(x, cudaStreamSynchronize(st));
+  NMC_TRY(reset_chain_state(x));
+  NMC_CUDA(x, cudaMemcpyAsync(x->dSign, p, C * sizeof(double), cudaMemcpyHostToDevice, st));
+  p += C * sizeof(double);
+  NMC_CUDA(x, cudaMemcpyAsync(x->dCounts, p, 3 * C * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  p += 3 * C * sizeof(uint64_t);
+  NMC_CUDA(x, cudaMemcpyAsync(x->dDrift, p, C * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  p += C * sizeof(uint64_t);
+  NMC_CUDA(x, cudaStreamSynchronize(st));
+  NMC_TRY(ensure_series(x, ns));
+  if (nser)
+    NMC_CUDA(x, cudaMemcpyAsync(x->dSeries, p, nser * sizeof(double), cudaMemcpyHostToDevice, st));
+  x->n_series = ns;
+  x->sweep_counter = h[5];
+  x->phase = h[6];
+  build_stacks(x, x->phase % 2 == 0);
+  NMC_CUDA(x, cudaGetLastError());
+  NMC_CUDA(x, cudaStreamSynchronize(st));
+  x->have_fields = true;
+  return NMC_OK;
+}
+
+nmc_status nmc_expk(int Lx, int Ly, double t, double c, double* out) {
+  if (!out || Lx < 1 || Ly < 1 || Lx * Ly > 1024) return NMC_EINVAL;
+  std::vector<double> K, w, V, E;
+  nmc_host::hopping(Lx, Ly, t, K);
+  nmc_host::jacobi_eigh(Lx * Ly, K, w, V);
+  nmc_host::expk_from_eig(Lx * Ly, w, V, c, E);
+  std::memcpy(out, E.data(), E.size() * sizeof(double));
+  return NMC_OK;
+}
+
+void nmc_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                uint32_t out[4]) {
+  uint32_t c[4] = {c0, c1, c2, c3};
+  philox4x32_10(c, k0, k1);
+  for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+nmc_status nmc_philox_device(const uint32_t* d_c0, int n, uint32_t c1, uint32_t c2, uint32_t c3,
+                             uint32_t k0, uint32_t k1, uint32_t* d_out, void* cuda_stream) {
+  if (!d_c0 || !d_out || n < 0) return NMC_EINVAL;
+  philox_batch(d_c0, n, c1, c2, c3, k0, k1, d_out, (cudaStream_t)cuda_stream);
+  if (cudaGetLastError() != cudaSuccess) return NMC_ECUDA;
+  if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) return NMC_ECUDA;
+  return NMC_OK;
+}
+
+const char* nmc_last_error(const nmc_ctx* x) { return x ? x->err.c_str() : "null context"; }
+
+const char* nmc_version(void) { return "libnmc 0.1 (sm_103a)"; }
+
+void nmc_destroy(nmc_ctx* x) {
+  if (!x) return;
+  if (x->device >= 0) cudaSetDevice(x->device);
+  free_all(x);
+  delete x;
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Internal declarations shared by the libnmc translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nmc {
+
+// ---------------------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies with the
+// published multipliers, key bumped by the Weyl constants between rounds.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+constexpr uint32_t kTagFlip = 0u;
+constexpr uint32_t kTagInit = 1u;
+
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * c[0];
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+}
+
+// ---------------------------------------------------------------------------- scaling
+// Diagonal scale vectors applied inside the batched GEMMs. Batch index b = 2*chain + spin.
+enum ScaleKind : int {
+  SC_NONE = 0,
+  SC_VEC = 1,        // v[i]
+  SC_INV_MAX1 = 2,   // 1 / max(v[i], 1)      (D_big^{-1} of a UDT split)
+  SC_MIN1 = 3,       // min(v[i], 1)          (D_small of a UDT split)
+  SC_FIELD = 4,      // e^{ sigma lam s(i,l)}
+  SC_FIELD_INV = 5   // e^{-sigma lam s(i,l)}
+};
+
+struct ScaleDesc {
+  int kind = SC_NONE;
+  const double* vec = nullptr;   // SC_VEC/INV_MAX1/MIN1: v + b*vstride
+  long long vstride = 0;
+  const int8_t* fields = nullptr;  // SC_FIELD*: fields + chain*fstride (already + l*N)
+  long long fstride = 0;
+  double e_lam = 1.0, e_mlam = 1.0;  // e^{lam}, e^{-lam}
+};
+
+__device__ __forceinline__ double scale_at(const ScaleDesc& d, int b, int i) {
+  switch (d.kind) {
+    case SC_VEC: return d.vec[b * d.vstride + i];
+    case SC_INV_MAX1: return 1.0 / fmax(d.vec[b * d.vstride + i], 1.0);
+    case SC_MIN1: return fmin(d.vec[b * d.vstride + i], 1.0);
+    case SC_FIELD:
+    case SC_FIELD_INV: {
+      const int s = d.fields[(long long)(b >> 1) * d.fstride + i];
+      const bool up = (b & 1) == 0;
+      bool pos = (s > 0) == up;          // sigma * s > 0
+      if (d.kind == SC_FIELD_INV) pos = !pos;
+      return pos ? d.e_lam : d.e_mlam;
+    }
+    default: return 1.0;
+  }
+}
+
+// ---------------------------------------------------------------------------- GEMM
+// C[b] = crow .* (op(A[b]) * (brow .* op(B[b]) .* bcol)) .* ccol + beta * Cin[b]
+// op(A): M x K, op(B): K x N. Optional: write a float copy (Cf), record per-chain
+// max |C - ref| (drift) into an array of doubles (as ordered bit patterns).
+template <typename T>
+struct GemmArgs {
+  int M = 0, N = 0, K = 0, batch = 0;
+  const T* A = nullptr; long long sA = 0; int lda = 0; int transA = 0;
+  const T* B = nullptr; long long sB = 0; int ldb = 0; int transB = 0;
+  T* C = nullptr; long long sC = 0; int ldc = 0;
+  const T* Cin = nullptr; long long sCin = 0; int ldcin = 0; double beta = 0.0;
+  ScaleDesc brow, bcol, crow, ccol;
+  float* Cf = nullptr; long long sCf = 0;           // float copy, ld = ldc
+  const void* ref = nullptr; int ref_is_float = 0;  // drift reference, ld = ldc, stride sC
+  long long sRef = 0;
+  unsigned long long* drift = nullptr;              // per chain: bits of max |C - ref|
+};
+
+void gemm(const GemmArgs<double>& g, cudaStream_t st);
+void gemm(const GemmArgs<float>& g, cudaStream_t st);
+
+// ---------------------------------------------------------------------------- UDT
+// Column-pivoted Householder QR of X[b] (N x N row-major): X P = Q R. Writes Q (U),
+// D = |diag R| and Tp = D^{-1} R P^T. ws: per-matrix global workspace of 2*N*N doubles
+// (used when the matrix does not fit in shared memory).
+void qrp_udt(const double* X, double* U, double* D, double* Tp, double* ws, int N, int batch,
+             cudaStream_t st);
+
+// Y[b] = X[b]^{-1} * (diag(1/max(DR,1)) * UR[b]^T) by Gauss-Jordan with partial pivoting.
+void solve_stab(const double* X, const double* UR, long long sUR, const double* DR,
+                long long sDR, double* Y, double* ws, int N, int batch, cudaStream_t st);
+
+// ---------------------------------------------------------------------------- flips
+template <typename T>
+struct FlipArgs {
+  T* G;                      // [chain][spin][N][N]
+  int8_t* fields;            // [chain][L][N]
+  int N, L, l;               // slice l
+  int kk;                    // delay
+  int g_in_smem;
+  uint32_t key0, key1, sweep;
+  long long chain_offset;
+  double dm, dp;             // e^{-2 lam} - 1, e^{2 lam} - 1
+  double* sign;              // per chain
+  unsigned long long* counts;  // per chain: attempts, accepts, disagreements
+  const uint8_t* replay;     // [chain][L][N] or null
+  T* panels_g;               // unused (panels live in shared memory)
+};
+template <typename T> void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st);
+size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem);
+
+// ---------------------------------------------------------------------------- misc
+void init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0, uint32_t k1,
+                 long long chain_offset, cudaStream_t st);
+void set_identity_batch(double* U, double* D, double* T, int N, int batch, cudaStream_t st);
+void copy_to_float(const double* x, float* y, long long n, cudaStream_t st);
+void copy_to_double(const float* x, double* y, long long n, cudaStream_t st);
+void fields_normalize(int8_t* s, long long n, cudaStream_t st);
+void philox_batch(const uint32_t* c0, int n, uint32_t c1, uint32_t c2, uint32_t c3,
+                  uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st);
+
+// Measurement on Gt = e^{dtau K/2} G e^{-dtau K/2}: adds per-chain sums of
+// (energy, ekin, double_occ, s_pipi, density) * sign and sign into acc[chain][8].
+constexpr int kNumObs = 6;   // energy, ekin, docc, s_pipi, density, sign
+void measure(const double* Gt, const double* K, const double* sign, int Lx, int Ly, double U,
+             double* acc, int n_chains, cudaStream_t st);
+
+}  // namespace nmc

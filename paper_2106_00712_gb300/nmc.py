@@ -1,0 +1,290 @@
+"""ctypes binding of libnmc (include/nmc.h): argument marshalling only.
+
+Every function named ``nmc_*`` here calls the C entry point of the same name; failures
+raise ``NmcError`` carrying the status and ``nmc_last_error``. All compute runs in the
+library's CUDA kernels; there is no fallback: if ``libnmc.so`` is missing or cannot be
+loaded, ``load()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnmc.so")
+
+NMC_OK, NMC_EINVAL, NMC_ENOMEM, NMC_ECUDA, NMC_ENUMERIC, NMC_ETIMEOUT, NMC_ESTATE = range(7)
+STATUS_NAMES = {0: "NMC_OK", 1: "NMC_EINVAL", 2: "NMC_ENOMEM", 3: "NMC_ECUDA",
+                4: "NMC_ENUMERIC", 5: "NMC_ETIMEOUT", 6: "NMC_ESTATE"}
+NMC_FP64, NMC_FP32 = 0, 1
+
+# every symbol include/nmc.h declares
+EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_fields",
+            "nmc_set_fields_device", "nmc_generate", "nmc_sweep", "nmc_sweep_replay",
+            "nmc_measure", "nmc_get_fields", "nmc_get_green", "nmc_get_dims",
+            "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_philox", "nmc_philox_device",
+            "nmc_last_error", "nmc_version", "nmc_destroy")
+
+
+class NmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("n_chains", ctypes.c_int), ("delay_k", ctypes.c_int),
+                ("precision", ctypes.c_int), ("drift_tol", ctypes.c_double),
+                ("chain_offset", ctypes.c_longlong), ("cuda_stream", ctypes.c_void_p)]
+
+
+class Est(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("err", ctypes.c_double)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("energy", Est), ("ekin", Est), ("double_occ", Est), ("s_pipi", Est),
+                ("density", Est), ("sign", Est), ("accept", ctypes.c_double),
+                ("max_drift", ctypes.c_double), ("n_meas", ctypes.c_longlong),
+                ("n_disagree", ctypes.c_longlong)]
+
+    def as_dict(self):
+        out = {}
+        for k in ("energy", "ekin", "double_occ", "s_pipi", "density", "sign"):
+            e = getattr(self, k)
+            out[k] = (e.mean, e.err)
+        for k in ("accept", "max_drift", "n_meas", "n_disagree"):
+            out[k] = getattr(self, k)
+        return out
+
+
+_lib = None
+
+
+def load():
+    """Load libnmc.so (raises OSError/FileNotFoundError if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FileNotFoundError(f"{LIB_PATH} not built: run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    u32 = ctypes.c_uint32
+    sig = {
+        "nmc_create": (i, [i, i, d, d, d, d, i, ctypes.c_uint64, P(vp)]),
+        "nmc_configure": (i, [vp, P(Options)]),
+        "nmc_default_options": (None, [P(Options)]),
+        "nmc_set_fields": (i, [vp, vp, sz]),
+        "nmc_set_fields_device": (i, [vp, vp, sz]),
+        "nmc_generate": (i, [vp, i, vp]),
+        "nmc_sweep": (i, [vp, i, i]),
+        "nmc_sweep_replay": (i, [vp, vp, sz, i]),
+        "nmc_measure": (i, [vp, vp, P(Obs)]),
+        "nmc_get_fields": (i, [vp, vp, sz]),
+        "nmc_get_green": (i, [vp, i, i, vp]),
+        "nmc_get_dims": (i, [vp, P(i), P(i), P(i), P(i)]),
+        "nmc_checkpoint": (i, [vp, vp, P(sz)]),
+        "nmc_restore": (i, [vp, vp, sz]),
+        "nmc_expk": (i, [i, i, d, d, vp]),
+        "nmc_philox": (None, [u32, u32, u32, u32, u32, u32, P(u32)]),
+        "nmc_philox_device": (i, [vp, i, u32, u32, u32, u32, u32, vp, vp]),
+        "nmc_last_error": (ctypes.c_char_p, [vp]),
+        "nmc_version": (ctypes.c_char_p, []),
+        "nmc_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, status):
+    if status != NMC_OK:
+        msg = load().nmc_last_error(ctx) if ctx else b""
+        raise NmcError(status, (msg or b"").decode())
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ------------------------------------------------------------------ raw entry points
+
+def nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed):
+    ctx = ctypes.c_void_p()
+    st = load().nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed, ctypes.byref(ctx))
+    if st != NMC_OK:
+        raise NmcError(st, "nmc_create rejected its arguments")
+    return ctx
+
+
+def nmc_default_options():
+    o = Options()
+    load().nmc_default_options(ctypes.byref(o))
+    return o
+
+
+def nmc_configure(ctx, opts=None):
+    _check(ctx, load().nmc_configure(ctx, ctypes.byref(opts) if opts is not None else None))
+
+
+def nmc_set_fields(ctx, s):
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    _check(ctx, load().nmc_set_fields(ctx, _ptr(s), s.size))
+
+
+def nmc_set_fields_device(ctx, dev_ptr, n):
+    _check(ctx, load().nmc_set_fields_device(ctx, ctypes.c_void_p(dev_ptr), n))
+
+
+def nmc_generate(ctx, mode=0, model=None):
+    _check(ctx, load().nmc_generate(ctx, mode, model))
+
+
+def nmc_sweep(ctx, n_sweeps, measure=1):
+    _check(ctx, load().nmc_sweep(ctx, n_sweeps, measure))
+
+
+def nmc_sweep_replay(ctx, accept, measure=1):
+    a = np.ascontiguousarray(accept, dtype=np.uint8)
+    _check(ctx, load().nmc_sweep_replay(ctx, _ptr(a), a.size, measure))
+
+
+def nmc_get_dims(ctx):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(ctx, load().nmc_get_dims(ctx, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def nmc_measure(ctx, per_chain=False):
+    _, _, n_chains, _ = nmc_get_dims(ctx)
+    pooled = Obs()
+    pc = (Obs * n_chains)() if per_chain else None
+    _check(ctx, load().nmc_measure(ctx, ctypes.cast(pc, ctypes.c_void_p) if pc else None,
+                                   ctypes.byref(pooled)))
+    return (pooled, list(pc)) if per_chain else pooled
+
+
+def nmc_get_fields(ctx):
+    N, L, C, _ = nmc_get_dims(ctx)
+    s = np.empty((C, L, N), dtype=np.int8)
+    _check(ctx, load().nmc_get_fields(ctx, _ptr(s), s.size))
+    return s
+
+
+def nmc_get_green(ctx, chain, spin):
+    N, _, _, _ = nmc_get_dims(ctx)
+    G = np.empty((N, N), dtype=np.float64)
+    _check(ctx, load().nmc_get_green(ctx, chain, spin, _ptr(G)))
+    return G
+
+
+def nmc_checkpoint(ctx):
+    n = ctypes.c_size_t(0)
+    _check(ctx, load().nmc_checkpoint(ctx, None, ctypes.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(ctx, load().nmc_checkpoint(ctx, _ptr(buf), ctypes.byref(n)))
+    return buf.tobytes()
+
+
+def nmc_restore(ctx, blob):
+    buf = np.frombuffer(blob, dtype=np.uint8).copy()
+    _check(ctx, load().nmc_restore(ctx, _ptr(buf), buf.size))
+
+
+def nmc_expk(Lx, Ly, t, c):
+    out = np.empty((Lx * Ly, Lx * Ly), dtype=np.float64)
+    st = load().nmc_expk(Lx, Ly, t, c, _ptr(out))
+    if st != NMC_OK:
+        raise NmcError(st, "nmc_expk")
+    return out
+
+
+def nmc_philox(c0, c1, c2, c3, k0, k1):
+    out = (ctypes.c_uint32 * 4)()
+    load().nmc_philox(c0, c1, c2, c3, k0, k1, out)
+    return list(out)
+
+
+def nmc_philox_device(d_c0_ptr, n, c1, c2, c3, k0, k1, d_out_ptr, stream=None):
+    st = load().nmc_philox_device(ctypes.c_void_p(d_c0_ptr), n, c1, c2, c3, k0, k1,
+                                  ctypes.c_void_p(d_out_ptr), stream)
+    if st != NMC_OK:
+        raise NmcError(st, "nmc_philox_device")
+
+
+def nmc_destroy(ctx):
+    load().nmc_destroy(ctx)
+
+
+def nmc_version():
+    return load().nmc_version().decode()
+
+
+# ------------------------------------------------------------------ convenience
+
+class Context:
+    """Owning wrapper: ``with Context(...) as c: c.generate(); c.sweep(10)``."""
+
+    def __init__(self, Lx, Ly, t, U, beta, dtau, n_wrap, seed=0, n_chains=1, delay_k=16,
+                 precision=NMC_FP64, drift_tol=0.0, chain_offset=0, stream=None):
+        self.ctx = nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed)
+        o = nmc_default_options()
+        o.n_chains, o.delay_k, o.precision = n_chains, delay_k, precision
+        o.drift_tol, o.chain_offset = drift_tol, chain_offset
+        o.cuda_stream = stream
+        try:
+            nmc_configure(self.ctx, o)
+        except Exception:
+            nmc_destroy(self.ctx)
+            raise
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def close(self):
+        if self.ctx is not None:
+            nmc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    dims = property(lambda self: nmc_get_dims(self.ctx))
+
+    def set_fields(self, s):
+        nmc_set_fields(self.ctx, s)
+
+    def generate(self, mode=0):
+        nmc_generate(self.ctx, mode)
+
+    def sweep(self, n, measure=1):
+        nmc_sweep(self.ctx, n, measure)
+
+    def sweep_replay(self, accept, measure=1):
+        nmc_sweep_replay(self.ctx, accept, measure)
+
+    def measure(self, per_chain=False):
+        return nmc_measure(self.ctx, per_chain)
+
+    def fields(self):
+        return nmc_get_fields(self.ctx)
+
+    def green(self, chain, spin):
+        return nmc_get_green(self.ctx, chain, spin)
+
+    def checkpoint(self):
+        return nmc_checkpoint(self.ctx)
+
+    def restore(self, blob):
+        nmc_restore(self.ctx, blob)
