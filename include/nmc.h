@@ -169,6 +169,24 @@ nmc_status nmc_philox_device(const uint32_t* d_c0, int n, uint32_t c1, uint32_t 
                              uint32_t c3, uint32_t k0, uint32_t k1, uint32_t* d_out,
                              void* cuda_stream);
 
+/* Per-kernel accounting (tracing). Every library kernel launch is counted by class
+ * ("gemm", "flip", "qrp", "solve", "measure", "other"). With profiling enabled, each
+ * launch is also bracketed by CUDA events on the context stream, and nmc_kernel_stats
+ * reports the summed device time of the bracketed launches. */
+typedef struct {
+  char name[16];
+  long long launches;    /* launches since the last reset                               */
+  long long timed;       /* launches bracketed by events                                */
+  double total_ms;       /* summed event time of the bracketed launches                 */
+} nmc_kernel_stat;
+
+/* Enable (1) or disable (0) event bracketing of launches. */
+nmc_status nmc_profile(nmc_ctx* ctx, int enable);
+
+/* Synchronise the stream and write up to `max` entries (one per kernel class) to `out`;
+ * *n receives the number of classes. reset != 0 clears the counters afterwards. */
+nmc_status nmc_kernel_stats(nmc_ctx* ctx, nmc_kernel_stat* out, int max, int* n, int reset);
+
 const char* nmc_last_error(const nmc_ctx* ctx);
 const char* nmc_version(void);
 void nmc_destroy(nmc_ctx* ctx);

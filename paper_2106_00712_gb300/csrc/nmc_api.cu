@@ -87,6 +87,15 @@ struct nmc_ctx {
   uint8_t* dReplay = nullptr;
   std::vector<void*> allocs;
 
+  // per-kernel accounting: launch counts always, CUDA-event brackets when prof is set
+  bool prof = false;
+  long long launches[6] = {0, 0, 0, 0, 0, 0};
+  long long timed[6] = {0, 0, 0, 0, 0, 0};
+  double total_ms[6] = {0, 0, 0, 0, 0, 0};
+  struct Rec { int cls; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> event_pool;
+
   cudaStream_t st() const { return (cudaStream_t)opt.cuda_stream; }
   int chains() const { return opt.n_chains; }
   int batch() const { return 2 * opt.n_chains; }
@@ -113,6 +122,49 @@ nmc_status fail(nmc_ctx* x, nmc_status s, const std::string& msg) {
     nmc_status s_ = (expr);        \
     if (s_ != NMC_OK) return s_;   \
   } while (0)
+
+enum KernelClass { KC_GEMM = 0, KC_FLIP, KC_QRP, KC_SOLVE, KC_MEASURE, KC_OTHER, KC_COUNT };
+const char* const kKernelClassNames[KC_COUNT] = {"gemm", "flip", "qrp", "solve", "measure",
+                                                 "other"};
+
+cudaEvent_t pool_event(nmc_ctx* x) {
+  if (!x->event_pool.empty()) {
+    cudaEvent_t e = x->event_pool.back();
+    x->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch through the accounting wrapper: count, and bracket with events when profiling.
+template <class F>
+void launch(nmc_ctx* x, int cls, F&& f) {
+  ++x->launches[cls];
+  if (!x->prof) {
+    f();
+    return;
+  }
+  cudaEvent_t a = pool_event(x), b = pool_event(x);
+  cudaEventRecord(a, x->st());
+  f();
+  cudaEventRecord(b, x->st());
+  x->recs.push_back({cls, a, b});
+}
+
+void resolve_events(nmc_ctx* x) {
+  for (auto& r : x->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      x->total_ms[r.cls] += ms;
+      ++x->timed[r.cls];
+    }
+    x->event_pool.push_back(r.a);
+    x->event_pool.push_back(r.b);
+  }
+  x->recs.clear();
+}
 
 void free_all(nmc_ctx* x) {
   for (void* p : x->allocs) cudaFree(p);
@@ -269,28 +321,28 @@ void wrap(nmc_ctx* x, int l, bool up) {
       auto g = gemm_base<float>(x, x->dEmf, 0, x->dGf, NN, x->dT1f);
       g.brow = field_scale(x, l, false);
       g.bcol = field_scale(x, l, true);
-      gemm(g, st);
-      gemm(gemm_base<float>(x, x->dT1f, NN, x->dEpf, 0, x->dGf), st);
+      launch(x, KC_GEMM, [&] { gemm(g, st); });
+      launch(x, KC_GEMM, [&] { gemm(gemm_base<float>(x, x->dT1f, NN, x->dEpf, 0, x->dGf), st); });
     } else {   // T1 = Ep G; G = e^-V (T1 Em) e^V
-      gemm(gemm_base<float>(x, x->dEpf, 0, x->dGf, NN, x->dT1f), st);
+      launch(x, KC_GEMM, [&] { gemm(gemm_base<float>(x, x->dEpf, 0, x->dGf, NN, x->dT1f), st); });
       auto g = gemm_base<float>(x, x->dT1f, NN, x->dEmf, 0, x->dGf);
       g.crow = field_scale(x, l, true);
       g.ccol = field_scale(x, l, false);
-      gemm(g, st);
+      launch(x, KC_GEMM, [&] { gemm(g, st); });
     }
   } else {
     if (up) {
       auto g = gemm_base<double>(x, x->dEm, 0, x->dG, NN, x->dT1);
       g.brow = field_scale(x, l, false);
       g.bcol = field_scale(x, l, true);
-      gemm(g, st);
-      gemm(gemm_base<double>(x, x->dT1, NN, x->dEp, 0, x->dG), st);
+      launch(x, KC_GEMM, [&] { gemm(g, st); });
+      launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dT1, NN, x->dEp, 0, x->dG), st); });
     } else {
-      gemm(gemm_base<double>(x, x->dEp, 0, x->dG, NN, x->dT1), st);
+      launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dEp, 0, x->dG, NN, x->dT1), st); });
       auto g = gemm_base<double>(x, x->dT1, NN, x->dEm, 0, x->dG);
       g.crow = field_scale(x, l, true);
       g.ccol = field_scale(x, l, false);
-      gemm(g, st);
+      launch(x, KC_GEMM, [&] { gemm(g, st); });
     }
   }
 }
@@ -302,12 +354,12 @@ void flip(nmc_ctx* x, int l, const uint8_t* replay) {
     FlipArgs<float> f{x->dGf, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                       (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
                       x->dCounts, replay, nullptr};
-    flip_slice(f, x->chains(), x->st());
+    launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   } else {
     FlipArgs<double> f{x->dG, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                        (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
                        x->dCounts, replay, nullptr};
-    flip_slice(f, x->chains(), x->st());
+    launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   }
 }
 
@@ -324,11 +376,11 @@ void stack_update(nmc_ctx* x, int j, const UDTView& src, const UDTBuf& dst, bool
     auto g = gemm_base<double>(x, x->dEm, 0, src.U, src.sU, X);
     g.brow = field_scale(x, l0, false);
     g.bcol = vec_scale(src.D, src.sD, SC_VEC);
-    gemm(g, st);
+    launch(x, KC_GEMM, [&] { gemm(g, st); });
     for (int l = l0 + 1; l < l0 + w; ++l) {
       auto h = gemm_base<double>(x, x->dEm, 0, X, NN, X2);
       h.brow = field_scale(x, l, false);
-      gemm(h, st);
+      launch(x, KC_GEMM, [&] { gemm(h, st); });
       std::swap(X, X2);
     }
   } else {
@@ -336,16 +388,16 @@ void stack_update(nmc_ctx* x, int j, const UDTView& src, const UDTBuf& dst, bool
     auto g = gemm_base<double>(x, x->dEm, 0, src.U, src.sU, X);
     g.bcol = vec_scale(src.D, src.sD, SC_VEC);
     g.crow = field_scale(x, lt, false);
-    gemm(g, st);
+    launch(x, KC_GEMM, [&] { gemm(g, st); });
     for (int l = lt - 1; l >= j * w; --l) {
       auto h = gemm_base<double>(x, x->dEm, 0, X, NN, X2);
       h.crow = field_scale(x, l, false);
-      gemm(h, st);
+      launch(x, KC_GEMM, [&] { gemm(h, st); });
       std::swap(X, X2);
     }
   }
-  qrp_udt(X, dst.U, dst.D, x->dTp, x->dWS, x->N, x->batch(), st);
-  gemm(gemm_base<double>(x, x->dTp, NN, src.T, src.sT, dst.T), st);
+  launch(x, KC_QRP, [&] { qrp_udt(X, dst.U, dst.D, x->dTp, x->dWS, x->N, x->batch(), st); });
+  launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dTp, NN, src.T, src.sT, dst.T), st); });
 }
 
 // G = (I + R L)^{-1} with R = U_R D_R T_R, L^T = U_L D_L T_L:
@@ -358,14 +410,14 @@ void recompute(nmc_ctx* x, const UDTView& R, const UDTView& L, bool drift) {
   g1.transA = 1;
   g1.crow = vec_scale(R.D, R.sD, SC_INV_MAX1);
   g1.ccol = vec_scale(L.D, L.sD, SC_INV_MAX1);
-  gemm(g1, st);
+  launch(x, KC_GEMM, [&] { gemm(g1, st); });
   auto g2 = gemm_base<double>(x, R.T, R.sT, L.T, L.sT, x->dXs);
   g2.transB = 1;
   g2.crow = vec_scale(R.D, R.sD, SC_MIN1);
   g2.ccol = vec_scale(L.D, L.sD, SC_MIN1);
   g2.Cin = x->dM1; g2.sCin = NN; g2.ldcin = x->N; g2.beta = 1.0;
-  gemm(g2, st);
-  solve_stab(x->dXs, R.U, R.sU, R.D, R.sD, x->dY, x->dWS, x->N, x->batch(), st);
+  launch(x, KC_GEMM, [&] { gemm(g2, st); });
+  launch(x, KC_SOLVE, [&] { solve_stab(x->dXs, R.U, R.sU, R.D, R.sD, x->dY, x->dWS, x->N, x->batch(), st); });
   auto g3 = gemm_base<double>(x, L.U, L.sU, x->dY, NN, x->dG);
   g3.brow = vec_scale(L.D, L.sD, SC_INV_MAX1);
   if (drift) {
@@ -375,16 +427,16 @@ void recompute(nmc_ctx* x, const UDTView& R, const UDTView& L, bool drift) {
     g3.drift = x->dDrift;
   }
   if (x->fp32()) { g3.Cf = x->dGf; g3.sCf = NN; }
-  gemm(g3, st);
+  launch(x, KC_GEMM, [&] { gemm(g3, st); });
 }
 
 void measure_now(nmc_ctx* x) {
   cudaStream_t st = x->st();
   const long long NN = x->NN();
-  gemm(gemm_base<double>(x, x->dEph, 0, x->dG, NN, x->dT1), st);   // e^{dtau K/2} G
-  gemm(gemm_base<double>(x, x->dT1, NN, x->dEmh, 0, x->dM1), st);  // ... e^{-dtau K/2}
+  launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dEph, 0, x->dG, NN, x->dT1), st); });   // e^{dtau K/2} G
+  launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dT1, NN, x->dEmh, 0, x->dM1), st); });  // ... e^{-dtau K/2}
   double* acc = x->dSeries + x->n_series * (long long)x->chains() * 8;
-  nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), st);
+  launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), st); });
 }
 
 void sweep_up(nmc_ctx* x, bool meas, const uint8_t* replay) {
@@ -624,7 +676,7 @@ nmc_status nmc_set_fields_device(nmc_ctx* x, const int8_t* d_s, size_t n) {
   if (n != need) return fail(x, NMC_EINVAL, "nmc_set_fields_device: size mismatch");
   NMC_TRY(ensure_configured(x));
   NMC_CUDA(x, cudaMemcpyAsync(x->dS, d_s, n, cudaMemcpyDeviceToDevice, x->st()));
-  fields_normalize(x->dS, (long long)n, x->st());
+  launch(x, KC_OTHER, [&] { fields_normalize(x->dS, (long long)n, x->st()); });
   return after_fields(x);
 }
 
@@ -633,8 +685,10 @@ nmc_status nmc_generate(nmc_ctx* x, int mode, const void* model) {
   if (!x) return NMC_EINVAL;
   if (mode != 0) return fail(x, NMC_EINVAL, "nmc_generate: only mode 0 (random) is available");
   NMC_TRY(ensure_configured(x));
-  init_fields(x->dS, x->chains(), x->Lt, x->N, (uint32_t)(x->seed & 0xffffffffu),
-              (uint32_t)(x->seed >> 32), x->opt.chain_offset, x->st());
+  launch(x, KC_OTHER, [&] {
+    init_fields(x->dS, x->chains(), x->Lt, x->N, (uint32_t)(x->seed & 0xffffffffu),
+                (uint32_t)(x->seed >> 32), x->opt.chain_offset, x->st());
+  });
   NMC_CUDA(x, cudaGetLastError());
   return after_fields(x);
 }
@@ -891,6 +945,32 @@ nmc_status nmc_philox_device(const uint32_t* d_c0, int n, uint32_t c1, uint32_t 
   return NMC_OK;
 }
 
+nmc_status nmc_profile(nmc_ctx* x, int enable) {
+  if (!x) return NMC_EINVAL;
+  x->prof = enable != 0;
+  return NMC_OK;
+}
+
+nmc_status nmc_kernel_stats(nmc_ctx* x, nmc_kernel_stat* out, int max, int* n, int reset) {
+  if (!x || (max > 0 && !out)) return NMC_EINVAL;
+  if (x->configured) {
+    NMC_CUDA(x, cudaSetDevice(x->device));
+    NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  }
+  resolve_events(x);
+  for (int c = 0; c < KC_COUNT && c < max; ++c) {
+    std::memset(out[c].name, 0, sizeof out[c].name);
+    std::strncpy(out[c].name, kKernelClassNames[c], sizeof out[c].name - 1);
+    out[c].launches = x->launches[c];
+    out[c].timed = x->timed[c];
+    out[c].total_ms = x->total_ms[c];
+  }
+  if (n) *n = KC_COUNT;
+  if (reset)
+    for (int c = 0; c < KC_COUNT; ++c) x->launches[c] = x->timed[c] = 0, x->total_ms[c] = 0;
+  return NMC_OK;
+}
+
 const char* nmc_last_error(const nmc_ctx* x) { return x ? x->err.c_str() : "null context"; }
 
 const char* nmc_version(void) { return "libnmc 0.1 (sm_103a)"; }
@@ -898,6 +978,12 @@ const char* nmc_version(void) { return "libnmc 0.1 (sm_103a)"; }
 void nmc_destroy(nmc_ctx* x) {
   if (!x) return;
   if (x->device >= 0) cudaSetDevice(x->device);
+  if (!x->recs.empty()) {
+    cudaStreamSynchronize(x->st());
+    resolve_events(x);
+  }
+  for (cudaEvent_t e : x->event_pool) cudaEventDestroy(e);
+  x->event_pool.clear();
   free_all(x);
   delete x;
 }

@@ -23,7 +23,8 @@ EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_field
             "nmc_set_fields_device", "nmc_generate", "nmc_sweep", "nmc_sweep_replay",
             "nmc_measure", "nmc_get_fields", "nmc_get_green", "nmc_get_dims",
             "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_philox", "nmc_philox_device",
-            "nmc_last_error", "nmc_version", "nmc_destroy")
+            "nmc_profile", "nmc_kernel_stats", "nmc_last_error", "nmc_version",
+            "nmc_destroy")
 
 
 class NmcError(RuntimeError):
@@ -58,6 +59,11 @@ class Obs(ctypes.Structure):
         return out
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_longlong),
+                ("timed", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -90,6 +96,8 @@ def load():
         "nmc_expk": (i, [i, i, d, d, vp]),
         "nmc_philox": (None, [u32, u32, u32, u32, u32, u32, P(u32)]),
         "nmc_philox_device": (i, [vp, i, u32, u32, u32, u32, u32, vp, vp]),
+        "nmc_profile": (i, [vp, i]),
+        "nmc_kernel_stats": (i, [vp, vp, i, P(i), i]),
         "nmc_last_error": (ctypes.c_char_p, [vp]),
         "nmc_version": (ctypes.c_char_p, []),
         "nmc_destroy": (None, [vp]),
@@ -217,6 +225,20 @@ def nmc_philox_device(d_c0_ptr, n, c1, c2, c3, k0, k1, d_out_ptr, stream=None):
         raise NmcError(st, "nmc_philox_device")
 
 
+def nmc_profile(ctx, enable):
+    _check(ctx, load().nmc_profile(ctx, int(bool(enable))))
+
+
+def nmc_kernel_stats(ctx, reset=False):
+    """{class: (launches, timed launches, total event ms)}"""
+    arr = (KernelStat * 16)()
+    n = ctypes.c_int(0)
+    _check(ctx, load().nmc_kernel_stats(ctx, ctypes.cast(arr, ctypes.c_void_p), 16,
+                                        ctypes.byref(n), int(bool(reset))))
+    return {arr[k].name.decode(): (arr[k].launches, arr[k].timed, arr[k].total_ms)
+            for k in range(n.value)}
+
+
 def nmc_destroy(ctx):
     load().nmc_destroy(ctx)
 
@@ -288,3 +310,9 @@ class Context:
 
     def restore(self, blob):
         nmc_restore(self.ctx, blob)
+
+    def profile(self, enable):
+        nmc_profile(self.ctx, enable)
+
+    def kernel_stats(self, reset=False):
+        return nmc_kernel_stats(self.ctx, reset)
