@@ -187,6 +187,30 @@ nmc_status nmc_profile(nmc_ctx* ctx, int enable);
  * *n receives the number of classes. reset != 0 clears the counters afterwards. */
 nmc_status nmc_kernel_stats(nmc_ctx* ctx, nmc_kernel_stat* out, int max, int* n, int reset);
 
+/* Equal-time Green's functions G_0 = (I + B_{L-1}...B_0)^{-1} of each chain and spin from
+ * caller-given fields, WITHOUT allocating: no cudaMalloc, cudaFree or other allocating
+ * call. The paper has no counterpart; this exists for callers that cannot allocate device
+ * memory when they need G (a caller whose memory pool or arena owns the device budget, or
+ * a runtime that forbids allocator calls after start-up). Computes what nmc_set_fields
+ * computes for G, with the same kernels in the same order.
+ *   N, L_tau, n_wrap: sites, slices, stabilization interval (L_tau % n_wrap == 0);
+ *   lam: HS coupling, cosh(lam) = e^{dtau U / 2};
+ *   d_expK_m: device, N x N row-major e^{-dtau K} (e.g. from nmc_expk(..., -dtau, ...));
+ *   d_fields: device, int8 [n_chains][L_tau][N], values +-1;
+ *   d_G: device output, [n_chains][2][N][N] row-major (spin 0 = up).
+ * Work is enqueued on cuda_stream (NULL = legacy default stream); outputs are valid once
+ * the stream reaches that point. Scratch: a fixed array of 4,194,304 doubles (32 MiB) in
+ * the library, held by every GPU that loads it until exit. Chains are processed in chunks
+ * that fit; one chain needs 20 N^2 + 4 N doubles (24 N^2 + 4 N when N > 111), so
+ * NMC_EINVAL is returned, before any work is enqueued, when that exceeds the array
+ * (N > 409), and for invalid arguments. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call shares the one array and overwrites it: calls
+ * whose work overlaps on the GPU (other streams, other threads) race -- serialise them. */
+nmc_status nmc_green_noalloc(int N, int L_tau, int n_wrap, double lam, const double* d_expK_m,
+                             const int8_t* d_fields, int n_chains, double* d_G,
+                             void* cuda_stream);
+
 const char* nmc_last_error(const nmc_ctx* ctx);
 const char* nmc_version(void);
 void nmc_destroy(nmc_ctx* ctx);

@@ -23,8 +23,8 @@ EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_field
             "nmc_set_fields_device", "nmc_generate", "nmc_sweep", "nmc_sweep_replay",
             "nmc_measure", "nmc_get_fields", "nmc_get_green", "nmc_get_dims",
             "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_philox", "nmc_philox_device",
-            "nmc_profile", "nmc_kernel_stats", "nmc_last_error", "nmc_version",
-            "nmc_destroy")
+            "nmc_profile", "nmc_kernel_stats", "nmc_green_noalloc", "nmc_last_error",
+            "nmc_version", "nmc_destroy")
 
 
 class NmcError(RuntimeError):
@@ -98,6 +98,7 @@ def load():
         "nmc_philox_device": (i, [vp, i, u32, u32, u32, u32, u32, vp, vp]),
         "nmc_profile": (i, [vp, i]),
         "nmc_kernel_stats": (i, [vp, vp, i, P(i), i]),
+        "nmc_green_noalloc": (i, [i, i, i, d, vp, vp, i, vp, vp]),
         "nmc_last_error": (ctypes.c_char_p, [vp]),
         "nmc_version": (ctypes.c_char_p, []),
         "nmc_destroy": (None, [vp]),
@@ -237,6 +238,17 @@ def nmc_kernel_stats(ctx, reset=False):
                                         ctypes.byref(n), int(bool(reset))))
     return {arr[k].name.decode(): (arr[k].launches, arr[k].timed, arr[k].total_ms)
             for k in range(n.value)}
+
+
+def nmc_green_noalloc(N, L_tau, n_wrap, lam, d_expK_ptr, d_fields_ptr, n_chains, d_G_ptr,
+                      stream=None):
+    """G_0 of every chain and spin from device fields into device d_G, using only the
+    library's fixed scratch array (no device allocation). Pointers are device addresses."""
+    st = load().nmc_green_noalloc(N, L_tau, n_wrap, lam, ctypes.c_void_p(d_expK_ptr),
+                                  ctypes.c_void_p(d_fields_ptr), n_chains,
+                                  ctypes.c_void_p(d_G_ptr), stream)
+    if st != NMC_OK:
+        raise NmcError(st, "nmc_green_noalloc")
 
 
 def nmc_destroy(ctx):
