@@ -4,8 +4,8 @@
 // k_qrp: Householder QR with column pivoting (Businger-Golub): at step p the remaining
 //   column of largest norm (lowest index on ties) is swapped into place, a reflector
 //   H_p = I - tau v v^T (v_p = 1) zeroes it below the diagonal, and the trailing columns
-//   are updated; column norms are downdated with the usual safeguard (recomputed when
-//   the downdated value has lost more than half its digits). Outputs U = Q (formed by
+//   are updated; squared column norms are downdated with the usual safeguard (recomputed
+//   when the downdated value has lost more than half its digits). Outputs U = Q (formed by
 //   backward accumulation of the reflectors), D = |diag R| and T = D^{-1} R P^T.
 // k_solve: Y = X^{-1} (Db_R^{-1} U_R^T) by Gauss-Jordan elimination with partial pivoting
 //   on the augmented matrix [X | RHS]; X is the well-scaled middle factor of the
@@ -41,7 +41,23 @@ __device__ __forceinline__ void warp_argmax(double& v, int& idx) {
   }
 }
 
-__host__ __device__ inline size_t qrp_small_bytes(int N) { return (size_t)N * (3 * sizeof(double) + sizeof(int)) + 64; }
+__host__ __device__ inline size_t qrp_small_bytes(int N) {
+  return (size_t)N * (3 * sizeof(double) + sizeof(int)) + 64;
+}
+
+// Four threads per column (a "quad", lanes 4q..4q+3 of a warp) for the trailing updates:
+// one warp covers 8 columns, so per-column scalar work costs one warp instruction per
+// 8 columns. Column norms are kept squared (n1 = current, n2 = at last recompute); the
+// LAPACK downdate safeguard "1 - (r/n1)^2 scaled by (n1/n2)^2 <= sqrt(eps)" is the same test
+// as n1^2 - r^2 <= sqrt(eps) n2^2, which needs no division or square root.
+constexpr int kQuad = 4;
+constexpr int kColsPerPass = kThreads / kQuad;
+
+__device__ __forceinline__ double quad_sum(double v, unsigned mask) {
+  v += __shfl_xor_sync(mask, v, 1);
+  v += __shfl_xor_sync(mask, v, 2);
+  return v;
+}
 
 __global__ void __launch_bounds__(kThreads)
 k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__ D,
@@ -49,9 +65,9 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   extern __shared__ __align__(16) unsigned char smraw[];
   const int b = blockIdx.x;
   const long long NN = (long long)N * N;
-  double* vn1 = (double*)smraw;
-  double* vn2 = vn1 + N;
-  double* tau = vn2 + N;
+  double* n1 = (double*)smraw;   // squared norms
+  double* n2 = n1 + N;
+  double* tau = n2 + N;
   int* perm = (int*)(tau + N);
   __shared__ int s_piv;
   double* W;  // column-major: W[c*N + r]
@@ -64,6 +80,8 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
     Q = W + NN;
   }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int sub = tid & (kQuad - 1);
+  const unsigned qmask = 0xFu << (lane & ~(kQuad - 1));
   const double* Xb = X + (long long)b * NN;
 
   for (long long e = tid; e < NN; e += kThreads) {
@@ -72,11 +90,14 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   }
   for (int c = tid; c < N; c += kThreads) perm[c] = c;
   __syncthreads();
-  for (int c = warp; c < N; c += kWarps) {
-    double s = 0.0;
-    for (int r = lane; r < N; r += 32) { const double v = W[(long long)c * N + r]; s += v * v; }
-    s = warp_sum(s);
-    if (lane == 0) { vn1[c] = sqrt(s); vn2[c] = vn1[c]; }
+  for (int c0 = 0; c0 < N; c0 += kColsPerPass) {
+    const int c = c0 + tid / kQuad;
+    if (c < N) {
+      double s = 0.0;
+      for (int r = sub; r < N; r += kQuad) { const double v = W[(long long)c * N + r]; s += v * v; }
+      s = quad_sum(s, qmask);
+      if (sub == 0) { n1[c] = s; n2[c] = s; }
+    }
   }
   __syncthreads();
 
@@ -86,7 +107,7 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
       double best = -1.0;
       int bi = N;
       for (int c = p + lane; c < N; c += 32)
-        if (vn1[c] > best) { best = vn1[c]; bi = c; }
+        if (n1[c] > best) { best = n1[c]; bi = c; }
       warp_argmax(best, bi);
       if (lane == 0) s_piv = bi;
     }
@@ -99,13 +120,13 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
         W[(long long)piv * N + r] = t0;
       }
       if (tid == 0) {
-        double t1 = vn1[p]; vn1[p] = vn1[piv]; vn1[piv] = t1;
-        t1 = vn2[p]; vn2[p] = vn2[piv]; vn2[piv] = t1;
+        double t1 = n1[p]; n1[p] = n1[piv]; n1[piv] = t1;
+        t1 = n2[p]; n2[p] = n2[piv]; n2[piv] = t1;
         const int ti = perm[p]; perm[p] = perm[piv]; perm[piv] = ti;
       }
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0) {  // reflector H_p = I - tau v v^T, v_p = 1, zeroing W[p+1:, p]
       double* col = W + (long long)p * N;
       const double alpha = col[p];
       double xn2 = 0.0;
@@ -125,36 +146,34 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
     __syncthreads();
     const double tp = tau[p];
     const double* v = W + (long long)p * N;
-    for (int c = p + 1 + warp; c < N; c += kWarps) {
-      double* col = W + (long long)c * N;
-      if (tp != 0.0) {
-        double dot = 0.0;
-        for (int r = p + 1 + lane; r < N; r += 32) dot += v[r] * col[r];
-        dot = warp_sum(dot) + col[p];
-        const double f = tp * dot;
-        for (int r = p + 1 + lane; r < N; r += 32) col[r] -= f * v[r];
-        __syncwarp();
-        if (lane == 0) col[p] -= f;
-        __syncwarp();
-      }
-      const double n1 = vn1[c];
-      if (n1 != 0.0) {
-        double temp = fabs(col[p]) / n1;
-        temp = fmax(0.0, 1.0 - temp * temp);
-        const double r12 = n1 / vn2[c];
-        const double temp2 = temp * r12 * r12;
-        double nv;
-        if (temp2 <= tol3z) {
-          double s = 0.0;
-          for (int r = p + 1 + lane; r < N; r += 32) s += col[r] * col[r];
-          s = warp_sum(s);
-          nv = sqrt(s);
-          if (lane == 0) { vn1[c] = nv; vn2[c] = nv; }
-        } else if (lane == 0) {
-          vn1[c] = n1 * sqrt(temp);
+    for (int c0 = p + 1; c0 < N; c0 += kColsPerPass) {
+      const int c = c0 + tid / kQuad;
+      if (c < N) {
+        double* col = W + (long long)c * N;
+        double rp = col[p];
+        if (tp != 0.0) {
+          double dot = 0.0;
+          for (int r = p + 1 + sub; r < N; r += kQuad) dot += v[r] * col[r];
+          dot = quad_sum(dot, qmask) + rp;
+          const double f = tp * dot;
+          for (int r = p + 1 + sub; r < N; r += kQuad) col[r] -= f * v[r];
+          rp -= f;
+          __syncwarp(qmask);
+          if (sub == 0) col[p] = rp;
+        }
+        const double a1 = n1[c];
+        if (a1 != 0.0) {
+          const double d = fma(-rp, rp, a1);
+          if (d <= tol3z * n2[c]) {
+            double s = 0.0;
+            for (int r = p + 1 + sub; r < N; r += kQuad) s += col[r] * col[r];
+            s = quad_sum(s, qmask);
+            if (sub == 0) { n1[c] = s; n2[c] = s; }
+          } else if (sub == 0) {
+            n1[c] = d;
+          }
         }
       }
-      __syncwarp();
     }
     __syncthreads();
   }
@@ -178,16 +197,18 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
     const double tp = tau[p];
     if (tp != 0.0) {
       const double* v = W + (long long)p * N;
-      for (int c = p + warp; c < N; c += kWarps) {
-        double* col = Q + (long long)c * N;
-        double dot = 0.0;
-        for (int r = p + 1 + lane; r < N; r += 32) dot += v[r] * col[r];
-        dot = warp_sum(dot) + col[p];
-        const double f = tp * dot;
-        for (int r = p + 1 + lane; r < N; r += 32) col[r] -= f * v[r];
-        __syncwarp();
-        if (lane == 0) col[p] -= f;
-        __syncwarp();
+      for (int c0 = p; c0 < N; c0 += kColsPerPass) {
+        const int c = c0 + tid / kQuad;
+        if (c < N) {
+          double* col = Q + (long long)c * N;
+          double dot = 0.0;
+          for (int r = p + 1 + sub; r < N; r += kQuad) dot += v[r] * col[r];
+          dot = quad_sum(dot, qmask) + col[p];
+          const double f = tp * dot;
+          for (int r = p + 1 + sub; r < N; r += kQuad) col[r] -= f * v[r];
+          __syncwarp(qmask);
+          if (sub == 0) col[p] -= f;
+        }
       }
     }
     __syncthreads();
