@@ -51,8 +51,11 @@ typedef enum {
 /* Arithmetic of the propagation steps. Ratios, acceptance, UDV stabilization, the
  * recomputed G and the measurements are always FP64. */
 typedef enum {
-  NMC_FP64 = 0,      /* flips, delayed updates and wraps in FP64                         */
-  NMC_FP32 = 1       /* flips, delayed updates and wraps in FP32 (FP32 accumulation)     */
+  NMC_FP64 = 0,      /* flips, delayed updates, wraps and stack products in FP64          */
+  NMC_FP32 = 1,      /* flips, delayed updates and wraps in FP32 (FP32 accumulation)      */
+  NMC_FP32X2 = 2     /* flips, delayed updates, wraps and stack products in compensated
+                        FP32 pairs (error-free products and sums, ~2^-44 relative) on the
+                        FP32 pipes; QR, recompute, ratios and measurement in FP64         */
 } nmc_precision;
 
 typedef struct {
@@ -60,7 +63,7 @@ typedef struct {
   int delay_k;           /* accepted flips folded per rank-k delayed update (>= 1) def. 16   */
   int precision;         /* nmc_precision                                        default 0  */
   double drift_tol;      /* NMC_ENUMERIC if max|G_wrapped - G_recomputed| exceeds this;
-                            <= 0 selects 1e-6 (FP64) or 1e-3 (FP32)              default 0  */
+                            <= 0 selects 1e-6 (FP64), 1e-3 (FP32), 1e-5 (FP32X2) default 0 */
   long long chain_offset;/* global index of local chain 0 (Philox counter word 2) def. 0   */
   void* cuda_stream;     /* cudaStream_t for all device work                     def. NULL */
 } nmc_options;
@@ -142,7 +145,7 @@ nmc_status nmc_get_fields(nmc_ctx* ctx, int8_t* s, size_t n);
 /* Copy the current equal-time G of one chain and spin (0 = up, 1 = down) to host
  * memory (N x N row-major). After an even number of sweeps since the fields were set,
  * G sits at slice 0, after an odd number at slice L_tau (equal to slice 0 cyclically).
- * In FP32 mode the FP32 G is widened. */
+ * In FP32 / FP32X2 mode the propagated G is widened to double. */
 nmc_status nmc_get_green(nmc_ctx* ctx, int chain, int spin, double* G);
 
 /* Sizes: N, L_tau, n_chains, effective delay (after the shared-memory clamp). */
@@ -170,7 +173,7 @@ nmc_status nmc_philox_device(const uint32_t* d_c0, int n, uint32_t c1, uint32_t 
                              void* cuda_stream);
 
 /* Per-kernel accounting (tracing). Every library kernel launch is counted by class
- * ("gemm", "flip", "qrp", "solve", "measure", "other"). With profiling enabled, each
+ * ("gemm", "flip", "qrp", "solve", "measure", "other", "gemm_df"). With profiling enabled, each
  * launch is also bracketed by CUDA events on the context stream, and nmc_kernel_stats
  * reports the summed device time of the bracketed launches. */
 typedef struct {

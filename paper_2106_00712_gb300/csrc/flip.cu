@@ -164,6 +164,161 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
   }
 }
 
+// Double-float variant. G0, the rank-k panels and every multiply-add are FP32 pairs
+// (df.cuh), and a running diagonal dg_j = G^_jj is updated with each accepted flip
+// (dg_j += a_m[j] b_m[j]), so an attempt reads G^_ii directly instead of reducing over
+// the panels. The acceptance is the FP64 decision u < |R|: R is first evaluated in
+// double-float (relative error ~1e-13); when |u - |R|| exceeds a margin of 1e-10 (|R| + 1)
+// that value decides, and only inside the margin is R recomputed in FP64 from the same
+// G^_ii -- both give the FP64 decision. The update coefficient -Delta/R^sigma uses a
+// double-float reciprocal.
+__device__ void flush_df(df2* G, const df2* Ap, const df2* Bp, int m, int N, int KK,
+                         long long NN) {
+  for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) {
+    const int sp = (int)(e / NN);
+    const long long rc = e - sp * NN;
+    const int r = (int)(rc / N), c = (int)(rc % N);
+    const df2* A_ = Ap + (long long)sp * KK * N;
+    const df2* B_ = Bp + (long long)sp * KK * N;
+    df2 acc = G[e];
+    for (int q = 0; q < m; ++q) df_fma_acc(acc, A_[q * N + r], B_[q * N + c]);
+    G[e] = df_finish(acc);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_accept;
+  __shared__ df2 s_coef[2];
+  __shared__ double s_sign;
+  __shared__ unsigned long long s_cnt[3];
+
+  const int c = blockIdx.x;
+  const int N = f.N, KK = f.kk;
+  const long long NN = (long long)N * N;
+  df2* Ap = (df2*)smraw;
+  df2* Bp = Ap + 2 * KK * N;
+  df2* dg = Bp + 2 * KK * N;          // running diagonal of G^, [2][N]
+  df2* Gs = dg + 2 * N;
+  // uniforms as FP32 pairs: u = x0 * 2^-32 has at most 32 significant bits, so the pair
+  // holds it exactly
+  df2* udf = (df2*)(((uintptr_t)(Gs + (f.g_in_smem ? 2 * NN : 0)) + 15) & ~(uintptr_t)15);
+  int8_t* sl = (int8_t*)(udf + N);
+
+  df2* Gg = f.G + (long long)c * 2 * NN;
+  df2* G = f.g_in_smem ? Gs : Gg;
+  int8_t* fl = f.fields + ((long long)c * f.L + f.l) * N;
+  const uint32_t gchain = (uint32_t)(f.chain_offset + c);
+  const uint8_t* rp = f.replay ? f.replay + ((long long)c * f.L + f.l) * N : nullptr;
+
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    sl[i] = fl[i];
+    uint32_t ctr[4] = {(uint32_t)(f.l * N + i), f.sweep, gchain, kTagFlip};
+    philox4x32_10(ctr, f.key0, f.key1);
+    udf[i] = df_from_double((double)ctr[0] * 2.3283064365386962890625e-10);  // 2^-32
+  }
+  if (f.g_in_smem)
+    for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) Gs[e] = Gg[e];
+  if (threadIdx.x == 0) {
+    s_sign = f.sign[c];
+    s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+    const int sp = i / N, r = i % N;
+    dg[i] = G[sp * NN + (long long)r * N + r];
+  }
+  __syncthreads();
+
+  const df2 one{1.f, 0.f};
+  int m = 0;
+  for (int i = 0; i < N; ++i) {
+    if (threadIdx.x == 0) {
+      const int s = sl[i];
+      const df2 gu = dg[i], gd = dg[N + i];
+      const df2 du = (s > 0) ? f.dm2 : f.dp2;  // e^{-2 lam s} - 1
+      const df2 dd = (s > 0) ? f.dp2 : f.dm2;  // e^{+2 lam s} - 1
+      const df2 Ru = df_add(one, df_mul(du, df_add(one, df_neg(gu))));
+      const df2 Rd = df_add(one, df_mul(dd, df_add(one, df_neg(gd))));
+      const df2 R = df_mul(Ru, Rd);
+      const df2 diff = df_add(udf[i], df_neg(df_abs(R)));
+      const float margin = 1e-10f * (fabsf(R.hi) + 1.f);
+      bool mine;
+      double Rsign = R.hi;
+      if (fabsf(diff.hi) > margin) {
+        mine = diff.hi < 0.f;
+      } else {  // certified FP64 evaluation from the same G^_ii
+        const double g64u = df_to_double(gu), g64d = df_to_double(gd);
+        const double d64u = (s > 0) ? f.dm : f.dp, d64d = (s > 0) ? f.dp : f.dm;
+        const double R64 = (1.0 + d64u * (1.0 - g64u)) * (1.0 + d64d * (1.0 - g64d));
+        mine = df_to_double(udf[i]) < fabs(R64);
+        Rsign = R64;
+      }
+      bool acc_flip = mine;
+      if (rp) {
+        acc_flip = rp[i] != 0;
+        if (acc_flip != mine) s_cnt[2]++;
+      }
+      s_cnt[0]++;
+      s_accept = acc_flip ? 1 : 0;
+      if (acc_flip) {
+        s_coef[0] = df_neg(df_mul(du, df_rcp(Ru)));
+        s_coef[1] = df_neg(df_mul(dd, df_rcp(Rd)));
+        if (Rsign < 0.0) s_sign = -s_sign;
+        s_cnt[1]++;
+        sl[i] = (int8_t)(-s);
+      }
+    }
+    __syncthreads();
+    if (s_accept) {
+      for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+        const int sp = t / N, r = t % N;
+        const df2* Gsp = G + sp * NN;
+        const df2* A_ = Ap + sp * KK * N;
+        const df2* B_ = Bp + sp * KK * N;
+        df2 ca = Gsp[(long long)r * N + i];   // column i of G^, row r
+        df2 rb = Gsp[(long long)i * N + r];   // row i of G^, column r
+        for (int q = 0; q < m; ++q) {
+          df_fma_acc(ca, A_[q * N + r], B_[q * N + i]);
+          df_fma_acc(rb, A_[q * N + i], B_[q * N + r]);
+        }
+        df2 v = df_neg(df_finish(ca));
+        if (r == i) v = df_add(v, one);
+        const df2 a = df_mul(s_coef[sp], v);
+        const df2 bb = df_finish(rb);
+        Ap[(sp * KK + m) * N + r] = a;
+        Bp[(sp * KK + m) * N + r] = bb;
+        dg[t] = df_add(dg[t], df_mul(a, bb));
+      }
+      ++m;
+      __syncthreads();
+      if (m == KK) {
+        flush_df(G, Ap, Bp, m, N, KK, NN);
+        m = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) {
+          const int sp = j / N, r = j % N;
+          dg[j] = G[sp * NN + (long long)r * N + r];
+        }
+        __syncthreads();
+      }
+    }
+  }
+  if (m > 0) {
+    flush_df(G, Ap, Bp, m, N, KK, NN);
+    __syncthreads();
+  }
+  if (f.g_in_smem)
+    for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) Gg[e] = Gs[e];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) fl[i] = sl[i];
+  if (threadIdx.x == 0) {
+    f.sign[c] = s_sign;
+    f.counts[3 * c + 0] += s_cnt[0];
+    f.counts[3 * c + 1] += s_cnt[1];
+    f.counts[3 * c + 2] += s_cnt[2];
+  }
+}
+
 }  // namespace
 
 size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem) {
@@ -183,5 +338,12 @@ void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st) {
 
 template void flip_slice<double>(const FlipArgs<double>&, int, cudaStream_t);
 template void flip_slice<float>(const FlipArgs<float>&, int, cudaStream_t);
+
+template <>
+void flip_slice<df2>(const FlipArgs<df2>& f, int n_chains, cudaStream_t st) {
+  const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(df2), f.g_in_smem);
+  cudaFuncSetAttribute(k_flip_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  k_flip_df<<<n_chains, kThreads, bytes, st>>>(f);
+}
 
 }  // namespace nmc

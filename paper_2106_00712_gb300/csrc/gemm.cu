@@ -96,13 +96,16 @@ k_gemm(const GemmArgs<T> g) {
       const T out = (T)v;
       const long long idx = (long long)gm * g.ldc + gn;
       if (g.ref) {
-        const double r = g.ref_is_float
-                             ? (double)((const float*)g.ref)[(long long)b * g.sRef + idx]
-                             : ((const double*)g.ref)[(long long)b * g.sRef + idx];
+        const long long ri = (long long)b * g.sRef + idx;
+        double r;
+        if (g.ref_is_float == 2) r = df_to_double(((const df2*)g.ref)[ri]);
+        else if (g.ref_is_float == 1) r = (double)((const float*)g.ref)[ri];
+        else r = ((const double*)g.ref)[ri];
         dmax = nan_max(dmax, fabs((double)out - r));
       }
       C[idx] = out;
       if (g.Cf) g.Cf[(long long)b * g.sCf + idx] = (float)out;
+      if (g.Cdf) g.Cdf[(long long)b * g.sCdf + idx] = df_from_double((double)out);
     }
   }
   if (g.drift) {

@@ -77,6 +77,8 @@ struct nmc_ctx {
   double *dG = nullptr, *dT1 = nullptr, *dX = nullptr, *dX2 = nullptr, *dTp = nullptr;
   double *dM1 = nullptr, *dXs = nullptr, *dY = nullptr, *dWS = nullptr;
   float *dGf = nullptr, *dT1f = nullptr;
+  df2 *dG2 = nullptr, *dT12 = nullptr, *dEm2 = nullptr, *dEp2 = nullptr;
+  df2 *dXa = nullptr, *dXb = nullptr, *dEmh2 = nullptr, *dEph2 = nullptr;
   std::vector<UDTBuf> slot;  // size nb + 1; entries 1..nb-1 allocated
   UDTBuf spare;
   double* dSign = nullptr;
@@ -89,9 +91,9 @@ struct nmc_ctx {
 
   // per-kernel accounting: launch counts always, CUDA-event brackets when prof is set
   bool prof = false;
-  long long launches[6] = {0, 0, 0, 0, 0, 0};
-  long long timed[6] = {0, 0, 0, 0, 0, 0};
-  double total_ms[6] = {0, 0, 0, 0, 0, 0};
+  long long launches[7] = {0, 0, 0, 0, 0, 0, 0};
+  long long timed[7] = {0, 0, 0, 0, 0, 0, 0};
+  double total_ms[7] = {0, 0, 0, 0, 0, 0, 0};
   struct Rec { int cls; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> event_pool;
@@ -101,6 +103,7 @@ struct nmc_ctx {
   int batch() const { return 2 * opt.n_chains; }
   long long NN() const { return (long long)N * N; }
   bool fp32() const { return opt.precision == NMC_FP32; }
+  bool dfp() const { return opt.precision == NMC_FP32X2; }
 };
 
 namespace {
@@ -123,9 +126,11 @@ nmc_status fail(nmc_ctx* x, nmc_status s, const std::string& msg) {
     if (s_ != NMC_OK) return s_;   \
   } while (0)
 
-enum KernelClass { KC_GEMM = 0, KC_FLIP, KC_QRP, KC_SOLVE, KC_MEASURE, KC_OTHER, KC_COUNT };
+enum KernelClass {
+  KC_GEMM = 0, KC_FLIP, KC_QRP, KC_SOLVE, KC_MEASURE, KC_OTHER, KC_GEMM_DF, KC_COUNT
+};
 const char* const kKernelClassNames[KC_COUNT] = {"gemm", "flip", "qrp", "solve", "measure",
-                                                 "other"};
+                                                 "other", "gemm_df"};
 
 cudaEvent_t pool_event(nmc_ctx* x) {
   if (!x->event_pool.empty()) {
@@ -174,6 +179,7 @@ void free_all(nmc_ctx* x) {
   x->dS = nullptr;
   x->dG = x->dT1 = x->dX = x->dX2 = x->dTp = x->dM1 = x->dXs = x->dY = x->dWS = nullptr;
   x->dGf = x->dT1f = nullptr;
+  x->dG2 = x->dT12 = x->dEm2 = x->dEp2 = x->dXa = x->dXb = x->dEmh2 = x->dEph2 = nullptr;
   x->slot.clear();
   x->spare = UDTBuf{};
   x->dSign = nullptr;
@@ -228,6 +234,16 @@ nmc_status alloc_all(nmc_ctx* x) {
     NMC_TRY(dalloc(x, &x->dGf, mats));
     NMC_TRY(dalloc(x, &x->dT1f, mats));
   }
+  if (x->dfp()) {
+    NMC_TRY(dalloc(x, &x->dEm2, NN));
+    NMC_TRY(dalloc(x, &x->dEp2, NN));
+    NMC_TRY(dalloc(x, &x->dG2, mats));
+    NMC_TRY(dalloc(x, &x->dT12, mats));
+    NMC_TRY(dalloc(x, &x->dXa, mats));
+    NMC_TRY(dalloc(x, &x->dXb, mats));
+    NMC_TRY(dalloc(x, &x->dEmh2, NN));
+    NMC_TRY(dalloc(x, &x->dEph2, NN));
+  }
   x->slot.assign(x->nb + 1, UDTBuf{});
   auto alloc_udt = [&](UDTBuf& u) -> nmc_status {
     NMC_TRY(dalloc(x, &u.U, mats));
@@ -252,6 +268,12 @@ nmc_status alloc_all(nmc_ctx* x) {
   if (x->fp32()) {
     copy_to_float(x->dEm, x->dEmf, NN, st);
     copy_to_float(x->dEp, x->dEpf, NN, st);
+  }
+  if (x->dfp()) {
+    split_to_df(x->dEm, x->dEm2, NN, st);
+    split_to_df(x->dEp, x->dEp2, NN, st);
+    split_to_df(x->dEmh, x->dEmh2, NN, st);
+    split_to_df(x->dEph, x->dEph2, NN, st);
   }
   NMC_CUDA(x, cudaGetLastError());
   NMC_CUDA(x, cudaStreamSynchronize(st));
@@ -307,6 +329,23 @@ GemmArgs<T> gemm_base(const nmc_ctx* x, const T* A, long long sA, const T* B, lo
   return g;
 }
 
+DfGemmArgs df_base(const nmc_ctx* x, const df2* A, long long sA, const df2* B, long long sB) {
+  DfGemmArgs g;
+  g.M = g.N = g.K = x->N;
+  g.batch = x->batch();
+  g.A = A; g.sA = sA; g.lda = x->N;
+  g.B = B; g.sB = sB; g.ldb = x->N;
+  g.sC = x->NN(); g.ldc = x->N;
+  g.fstride = (long long)x->Lt * x->N;
+  for (int m = -2; m <= 2; ++m) {
+    const double v = std::exp(m * x->lam);
+    const float hi = (float)v;
+    g.e[m + 2].hi = hi;
+    g.e[m + 2].lo = (float)(v - (double)hi);
+  }
+  return g;
+}
+
 UDTView identity_view(const nmc_ctx* x) { return UDTView{x->dI, 0, x->dOnes, 0, x->dI, 0}; }
 UDTView view_of(const nmc_ctx* x, const UDTBuf& b) {
   return UDTView{b.U, x->NN(), b.D, x->N, b.T, x->NN()};
@@ -316,6 +355,27 @@ UDTView view_of(const nmc_ctx* x, const UDTBuf& b) {
 void wrap(nmc_ctx* x, int l, bool up) {
   cudaStream_t st = x->st();
   const long long NN = x->NN();
+  if (x->dfp()) {
+    const int8_t* fl = x->dS + (long long)l * x->N;
+    if (up) {  // T1 = Em (e^V G e^-V); G = T1 Ep
+      DfGemmArgs g = df_base(x, x->dEm2, 0, x->dG2, NN);
+      g.C = x->dT12;
+      g.bfields = fl; g.br = 1; g.bc = -1;
+      launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
+      DfGemmArgs h = df_base(x, x->dT12, NN, x->dEp2, 0);
+      h.C = x->dG2;
+      launch(x, KC_GEMM_DF, [&] { gemm_df(h, st); });
+    } else {   // T1 = Ep G; G = e^-V (T1 Em) e^V
+      DfGemmArgs g = df_base(x, x->dEp2, 0, x->dG2, NN);
+      g.C = x->dT12;
+      launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
+      DfGemmArgs h = df_base(x, x->dT12, NN, x->dEm2, 0);
+      h.C = x->dG2;
+      h.cfields = fl; h.cr = -1; h.cc = 1;
+      launch(x, KC_GEMM_DF, [&] { gemm_df(h, st); });
+    }
+    return;
+  }
   if (x->fp32()) {
     if (up) {  // T1 = Em (e^V G e^-V); G = T1 Ep
       auto g = gemm_base<float>(x, x->dEmf, 0, x->dGf, NN, x->dT1f);
@@ -350,7 +410,18 @@ void wrap(nmc_ctx* x, int l, bool up) {
 void flip(nmc_ctx* x, int l, const uint8_t* replay) {
   const uint32_t k0 = (uint32_t)(x->seed & 0xffffffffu), k1 = (uint32_t)(x->seed >> 32);
   const double dm = std::exp(-2.0 * x->lam) - 1.0, dp = std::exp(2.0 * x->lam) - 1.0;
-  if (x->fp32()) {
+  if (x->dfp()) {
+    auto split = [](double v) {
+      df2 r;
+      r.hi = (float)v;
+      r.lo = (float)(v - (double)r.hi);
+      return r;
+    };
+    FlipArgs<df2> f{x->dG2, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
+                    (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
+                    x->dCounts, replay, nullptr, split(dm), split(dp)};
+    launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
+  } else if (x->fp32()) {
     FlipArgs<float> f{x->dGf, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                       (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
                       x->dCounts, replay, nullptr};
@@ -371,6 +442,36 @@ void stack_update(nmc_ctx* x, int j, const UDTView& src, const UDTBuf& dst, bool
   const int w = x->w;
   double* X = x->dX;
   double* X2 = x->dX2;
+  if (x->dfp()) {
+    // (B_block U) in double-float, then X = (B_block U) D in FP64 for the QR:
+    // right: B_block = B_{(j+1)w-1} ... B_{jw}; left (transposed): B_{jw}^T ... B_{(j+1)w-1}^T
+    const long long nsplit = src.sU ? NN * x->batch() : NN;
+    launch(x, KC_OTHER, [&] { split_to_df(src.U, x->dXa, nsplit, st); });
+    const df2* cur = x->dXa;
+    long long scur = src.sU ? NN : 0;
+    df2* bufs[2] = {x->dXb, x->dXa};
+    for (int k = 0; k < w; ++k) {
+      const int l = right ? j * w + k : (j + 1) * w - 1 - k;
+      const bool last = k == w - 1;
+      DfGemmArgs g = df_base(x, x->dEm2, 0, cur, scur);
+      const int8_t* fl = x->dS + (long long)l * x->N;
+      if (right) { g.bfields = fl; g.br = 1; }
+      else { g.cfields = fl; g.cr = 1; }
+      if (last) {
+        g.Cd = X;
+        g.colscale = src.D;
+        g.sColscale = src.sD;
+      } else {
+        g.C = bufs[k & 1];
+      }
+      launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
+      cur = bufs[k & 1];
+      scur = NN;
+    }
+    launch(x, KC_QRP, [&] { qrp_udt(X, dst.U, dst.D, x->dTp, x->dWS, x->N, x->batch(), st); });
+    launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dTp, NN, src.T, src.sT, dst.T), st); });
+    return;
+  }
   if (right) {
     const int l0 = j * w;
     auto g = gemm_base<double>(x, x->dEm, 0, src.U, src.sU, X);
@@ -421,21 +522,32 @@ void recompute(nmc_ctx* x, const UDTView& R, const UDTView& L, bool drift) {
   auto g3 = gemm_base<double>(x, L.U, L.sU, x->dY, NN, x->dG);
   g3.brow = vec_scale(L.D, L.sD, SC_INV_MAX1);
   if (drift) {
-    g3.ref = x->fp32() ? (const void*)x->dGf : (const void*)x->dG;
-    g3.ref_is_float = x->fp32() ? 1 : 0;
+    g3.ref = x->fp32() ? (const void*)x->dGf : x->dfp() ? (const void*)x->dG2 : (const void*)x->dG;
+    g3.ref_is_float = x->fp32() ? 1 : x->dfp() ? 2 : 0;
     g3.sRef = NN;
     g3.drift = x->dDrift;
   }
   if (x->fp32()) { g3.Cf = x->dGf; g3.sCf = NN; }
+  if (x->dfp()) { g3.Cdf = x->dG2; g3.sCdf = NN; }
   launch(x, KC_GEMM, [&] { gemm(g3, st); });
 }
 
 void measure_now(nmc_ctx* x) {
   cudaStream_t st = x->st();
   const long long NN = x->NN();
+  double* acc = x->dSeries + x->n_series * (long long)x->chains() * 8;
+  if (x->dfp()) {  // G~ = e^{dtau K/2} G e^{-dtau K/2} from the pair copy of the recomputed G
+    DfGemmArgs g = df_base(x, x->dEph2, 0, x->dG2, NN);
+    g.C = x->dT12;
+    launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
+    DfGemmArgs h = df_base(x, x->dT12, NN, x->dEmh2, 0);
+    h.Cd = x->dM1;
+    launch(x, KC_GEMM_DF, [&] { gemm_df(h, st); });
+    launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), st); });
+    return;
+  }
   launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dEph, 0, x->dG, NN, x->dT1), st); });   // e^{dtau K/2} G
   launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dT1, NN, x->dEmh, 0, x->dM1), st); });  // ... e^{-dtau K/2}
-  double* acc = x->dSeries + x->n_series * (long long)x->chains() * 8;
   launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), st); });
 }
 
@@ -546,7 +658,7 @@ nmc_status check_drift(nmc_ctx* x) {
                               cudaMemcpyDeviceToHost, x->st()));
   NMC_CUDA(x, cudaStreamSynchronize(x->st()));
   double tol = x->opt.drift_tol;
-  if (tol <= 0) tol = x->fp32() ? 1e-3 : 1e-6;
+  if (tol <= 0) tol = x->fp32() ? 1e-3 : x->dfp() ? 1e-5 : 1e-6;
   for (size_t c = 0; c < bits.size(); ++c) {
     double d;
     std::memcpy(&d, &bits[c], sizeof d);
@@ -652,7 +764,7 @@ nmc_status nmc_configure(nmc_ctx* x, const nmc_options* o) {
   nmc_options n;
   nmc_default_options(&n);
   if (o) n = *o;
-  if (n.n_chains < 1 || n.delay_k < 1 || (n.precision != NMC_FP64 && n.precision != NMC_FP32) ||
+  if (n.n_chains < 1 || n.delay_k < 1 || (n.precision != NMC_FP64 && n.precision != NMC_FP32 && n.precision != NMC_FP32X2) ||
       n.chain_offset < 0 || n.n_chains > (1 << 20))
     return fail(x, NMC_EINVAL, "invalid nmc_options");
   x->opt = n;
@@ -820,7 +932,13 @@ nmc_status nmc_get_green(nmc_ctx* x, int chain, int spin, double* G) {
   NMC_CUDA(x, cudaSetDevice(x->device));
   const long long NN = x->NN();
   const long long off = ((long long)chain * 2 + spin) * NN;
-  if (x->fp32()) {
+  if (x->dfp()) {
+    std::vector<df2> tmp(NN);
+    NMC_CUDA(x, cudaMemcpyAsync(tmp.data(), x->dG2 + off, NN * sizeof(df2),
+                                cudaMemcpyDeviceToHost, x->st()));
+    NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+    for (long long e = 0; e < NN; ++e) G[e] = (double)tmp[e].hi + (double)tmp[e].lo;
+  } else if (x->fp32()) {
     std::vector<float> tmp(NN);
     NMC_CUDA(x, cudaMemcpyAsync(tmp.data(), x->dGf + off, NN * sizeof(float),
                                 cudaMemcpyDeviceToHost, x->st()));

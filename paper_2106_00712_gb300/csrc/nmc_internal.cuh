@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df.cuh"
+
 namespace nmc {
 
 // ---------------------------------------------------------------------------- Philox
@@ -80,12 +82,32 @@ struct GemmArgs {
   ScaleDesc brow, bcol, crow, ccol;
   float* Cf = nullptr; long long sCf = 0;           // float copy, ld = ldc
   const void* ref = nullptr; int ref_is_float = 0;  // drift reference, ld = ldc, stride sC
-  long long sRef = 0;
+  long long sRef = 0;                               // (ref_is_float: 1 = float, 2 = df2)
   unsigned long long* drift = nullptr;              // per chain: bits of max |C - ref|
+  df2* Cdf = nullptr; long long sCdf = 0;           // double-float copy, ld = ldc
 };
 
 void gemm(const GemmArgs<double>& g, cudaStream_t st);
 void gemm(const GemmArgs<float>& g, cudaStream_t st);
+
+// Double-float GEMM (compensated FP32 pairs): C[b] = e^{V_c} (A[b] (e^{V_b} B[b])) e^{V_c'}
+// where the optional diagonal factors are field exponentials e^{m lam}, m = sigma *
+// (r * s(row) + c * s(col)) in {-2..2}, applied while staging B (br, bc) or in the
+// epilogue (cr, cc). Output either double-float (C) or FP64 (Cd, optionally times a
+// per-column FP64 scale colscale[b][n]).
+struct DfGemmArgs {
+  int M = 0, N = 0, K = 0, batch = 0;
+  const df2* A = nullptr; long long sA = 0; int lda = 0;
+  const df2* B = nullptr; long long sB = 0; int ldb = 0;
+  df2* C = nullptr; double* Cd = nullptr; long long sC = 0; int ldc = 0;
+  const double* colscale = nullptr; long long sColscale = 0;
+  const int8_t* bfields = nullptr; int br = 0, bc = 0;
+  const int8_t* cfields = nullptr; int cr = 0, cc = 0;
+  long long fstride = 0;
+  df2 e[5];  // e^{m lam}, m = -2..2
+};
+void gemm_df(const DfGemmArgs& g, cudaStream_t st);
+void split_to_df(const double* x, df2* y, long long n, cudaStream_t st);
 
 // ---------------------------------------------------------------------------- UDT
 // Column-pivoted Householder QR of X[b] (N x N row-major): X P = Q R. Writes Q (U),
@@ -113,6 +135,7 @@ struct FlipArgs {
   unsigned long long* counts;  // per chain: attempts, accepts, disagreements
   const uint8_t* replay;     // [chain][L][N] or null
   T* panels_g;               // unused (panels live in shared memory)
+  df2 dm2, dp2;              // dm, dp as FP32 pairs (compensated mode)
 };
 template <typename T> void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st);
 size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem);

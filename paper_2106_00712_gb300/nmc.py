@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libnmc.so")
 NMC_OK, NMC_EINVAL, NMC_ENOMEM, NMC_ECUDA, NMC_ENUMERIC, NMC_ETIMEOUT, NMC_ESTATE = range(7)
 STATUS_NAMES = {0: "NMC_OK", 1: "NMC_EINVAL", 2: "NMC_ENOMEM", 3: "NMC_ECUDA",
                 4: "NMC_ENUMERIC", 5: "NMC_ETIMEOUT", 6: "NMC_ESTATE"}
-NMC_FP64, NMC_FP32 = 0, 1
+NMC_FP64, NMC_FP32, NMC_FP32X2 = 0, 1, 2
 
 # every symbol include/nmc.h declares
 EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_fields",

@@ -40,12 +40,12 @@ def _ctx(nmc, model, **kw):
 
 
 def _compare_run(nmc, model, chains, n_sweeps, measure_from=0, delay_k=16, fields=None,
-                 check_chains=None, chain_offset=0):
+                 check_chains=None, chain_offset=0, precision=0, g_rel=G_REL):
     """Run n_sweeps on the GPU and on the oracle for the checked chains; compare the
     field after every sweep (bit-exact), G at the end and the accumulated observables."""
     check = list(range(chains)) if check_chains is None else check_chains
     with _ctx(nmc, model, n_chains=chains, delay_k=delay_k, chain_offset=chain_offset,
-              drift_tol=1e-3) as c:
+              drift_tol=1e-3, precision=precision) as c:
         if fields is None:
             c.generate()
             refs = {ch: Chain(model, initial_fields(model, ch + chain_offset), ch + chain_offset)
@@ -66,7 +66,7 @@ def _compare_run(nmc, model, chains, n_sweeps, measure_from=0, delay_k=16, field
                 assert np.array_equal(f[ch], refs[ch].s), f"decisions differ: sweep {sw} chain {ch}"
         for ch in check:
             for spin in (0, 1):
-                assert _rel(c.green(ch, spin), refs[ch].G[spin]) < G_REL
+                assert _rel(c.green(ch, spin), refs[ch].G[spin]) < g_rel
         if n_sweeps > measure_from:
             _, per = c.measure(per_chain=True)
             for ch in check:
@@ -224,6 +224,58 @@ def test_fp32_replay_follows_oracle_trajectory(nmc):
             want = refs[ch].means()
             for k in ("energy", "double_occ", "s_pipi", "density"):
                 assert abs(getattr(per[ch], k).mean - want[k]) < OBS_ABS, k
+
+
+# compensated FP32-pair propagation: ~2^-44 per operation, so G tracks FP64 to ~1e-10
+G_REL_X2 = 1e-8
+
+
+def test_fp32x2_replay_meets_accuracy_bar(nmc):
+    """FP32X2 on the oracle's trajectory: max|G - G_fp64| <= 1e-5 before every
+    stabilization (recorded drift against the FP64 recompute), G at the end within 1e-8
+    of the oracle's, no decision of its own differs, observables equal the oracle's."""
+    model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=0)
+    chains = 2
+    refs = [Chain(model, initial_fields(model, ch), ch) for ch in range(chains)]
+    with _ctx(nmc, model, n_chains=chains, precision=nmc.NMC_FP32X2) as c:
+        c.generate()
+        for sw in range(4):
+            before = np.stack([r.s.copy() for r in refs])
+            for r in refs:
+                r.sweep(True)
+            accept = (np.stack([r.s for r in refs]) != before).astype(np.uint8)
+            c.sweep_replay(accept, measure=1)
+            np.testing.assert_array_equal(c.fields(), np.stack([r.s for r in refs]))
+        obs, per = c.measure(per_chain=True)
+        assert obs.max_drift <= 1e-5, obs.max_drift
+        assert obs.n_disagree == 0
+        for ch in range(chains):
+            for spin in (0, 1):
+                assert _rel(c.green(ch, spin), refs[ch].G[spin]) < G_REL_X2
+            want = refs[ch].means()
+            for k in ("energy", "double_occ", "s_pipi", "density"):
+                assert abs(getattr(per[ch], k).mean - want[k]) < OBS_ABS, k
+
+
+def test_fp32x2_free_running_decisions_equal_oracle(nmc):
+    """Free-running FP32X2 chains make the oracle's decisions (4x4, 60 sweeps)."""
+    model = Model(4, 4, 1.0, 4.0, 2.0, 0.1, 10, seed=0)
+    _compare_run(nmc, model, chains=1, n_sweeps=60, measure_from=10,
+                 precision=nmc.NMC_FP32X2, g_rel=G_REL_X2)
+
+
+@pytest.mark.parametrize("Lx,Ly,n_wrap,k,chains", [
+    (2, 1, 2, 16, 2), (6, 6, 5, 5, 2), (10, 10, 5, 16, 2), (12, 12, 5, 8, 1)])
+def test_fp32x2_ragged_sizes(nmc, Lx, Ly, n_wrap, k, chains):
+    model = Model(Lx, Ly, 1.0, 4.0, 1.0, 0.1, n_wrap, seed=23)
+    _compare_run(nmc, model, chains=chains, n_sweeps=3, measure_from=1, delay_k=k,
+                 precision=nmc.NMC_FP32X2, g_rel=G_REL_X2)
+
+
+def test_fp32x2_8x8_256_chains_sampled(nmc):
+    model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=0)
+    _compare_run(nmc, model, chains=256, n_sweeps=2, measure_from=0, delay_k=16,
+                 check_chains=[3, 200], precision=nmc.NMC_FP32X2, g_rel=G_REL_X2)
 
 
 def test_state_errors_on_device(nmc):
