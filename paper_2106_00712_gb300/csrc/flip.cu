@@ -20,18 +20,26 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Thread t owns column c = t % N of rows t / N, t / N + rows_per_pass, ... of both spins:
+// 32-bit index arithmetic only, consecutive threads on consecutive columns.
 template <typename T>
 __device__ void flush(T* G, const T* Ap, const T* Bp, int m, int N, int KK, long long NN) {
   // G[sp][r][c] += sum_{q<m} A[sp][q][r] * B[sp][q][c]
-  for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) {
-    const int sp = (int)(e / NN);
-    const long long rc = e - sp * NN;
-    const int r = (int)(rc / N), c = (int)(rc % N);
-    const T* A_ = Ap + (long long)sp * KK * N;
-    const T* B_ = Bp + (long long)sp * KK * N;
-    T v = G[e];
-    for (int q = 0; q < m; ++q) v = fma(A_[q * N + r], B_[q * N + c], v);
-    G[e] = v;
+  const int nthr = blockDim.x;
+  if ((int)threadIdx.x >= (nthr / N) * N && nthr >= N) return;
+  const int c0 = threadIdx.x % N, r0 = threadIdx.x / N;
+  const int rstep = nthr >= N ? nthr / N : 1;
+  for (int sp = 0; sp < 2; ++sp) {
+    const T* A_ = Ap + sp * KK * N;
+    const T* B_ = Bp + sp * KK * N;
+    T* Gs = G + sp * NN;
+    for (int c = c0; c < N; c += (nthr >= N ? N : nthr)) {
+      for (int r = (nthr >= N ? r0 : 0); r < N; r += rstep) {
+        T v = Gs[r * N + c];
+        for (int q = 0; q < m; ++q) v = fma(A_[q * N + r], B_[q * N + c], v);
+        Gs[r * N + c] = v;
+      }
+    }
   }
 }
 
@@ -174,15 +182,21 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
 // double-float reciprocal.
 __device__ void flush_df(df2* G, const df2* Ap, const df2* Bp, int m, int N, int KK,
                          long long NN) {
-  for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) {
-    const int sp = (int)(e / NN);
-    const long long rc = e - sp * NN;
-    const int r = (int)(rc / N), c = (int)(rc % N);
-    const df2* A_ = Ap + (long long)sp * KK * N;
-    const df2* B_ = Bp + (long long)sp * KK * N;
-    df2 acc = G[e];
-    for (int q = 0; q < m; ++q) df_fma_acc(acc, A_[q * N + r], B_[q * N + c]);
-    G[e] = df_finish(acc);
+  const int nthr = blockDim.x;
+  if ((int)threadIdx.x >= (nthr / N) * N && nthr >= N) return;
+  const int c0 = threadIdx.x % N, r0 = threadIdx.x / N;
+  const int rstep = nthr >= N ? nthr / N : 1;
+  for (int sp = 0; sp < 2; ++sp) {
+    const df2* A_ = Ap + sp * KK * N;
+    const df2* B_ = Bp + sp * KK * N;
+    df2* Gs = G + sp * NN;
+    for (int c = c0; c < N; c += (nthr >= N ? N : nthr)) {
+      for (int r = (nthr >= N ? r0 : 0); r < N; r += rstep) {
+        df2 acc = Gs[r * N + c];
+        for (int q = 0; q < m; ++q) df_fma_acc(acc, A_[q * N + r], B_[q * N + c]);
+        Gs[r * N + c] = df_finish(acc);
+      }
+    }
   }
 }
 

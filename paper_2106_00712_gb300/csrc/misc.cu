@@ -90,9 +90,9 @@ k_measure(const double* __restrict__ Gt, const double* __restrict__ K,
   const double* Gu = Gt + (long long)c * 2 * NN;
   const double* Gd = Gu + NN;
   double kin = 0.0, conn = 0.0;
-  for (long long e = threadIdx.x; e < NN; e += blockDim.x) {
-    const int i = (int)(e / N), j = (int)(e % N);
-    const long long ji = (long long)j * N + i;
+  for (int e = threadIdx.x; e < (int)NN; e += blockDim.x) {
+    const int i = e / N, j = e - i * N;
+    const int ji = j * N + i;
     kin += K[e] * (Gu[ji] + Gd[ji]);
     const double pij = (((i % Lx) + (i / Lx) + (j % Lx) + (j / Lx)) & 1) ? -1.0 : 1.0;
     const double dij = (i == j) ? 1.0 : 0.0;

@@ -84,9 +84,9 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   const unsigned qmask = 0xFu << (lane & ~(kQuad - 1));
   const double* Xb = X + (long long)b * NN;
 
-  for (long long e = tid; e < NN; e += kThreads) {
-    const int r = (int)(e / N), c = (int)(e % N);
-    W[(long long)c * N + r] = Xb[e];
+  for (int e = tid; e < (int)NN; e += kThreads) {
+    const int r = e / N, c = e - r * N;
+    W[c * N + r] = Xb[e];
   }
   for (int c = tid; c < N; c += kThreads) perm[c] = c;
   __syncthreads();
@@ -182,14 +182,14 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   double* Db = D + (long long)b * N;
   for (int r = tid; r < N; r += kThreads) Db[r] = fabs(W[(long long)r * N + r]);
   double* Tb = Tp + (long long)b * NN;
-  for (long long e = tid; e < NN; e += kThreads) {
-    const int r = (int)(e / N), c = (int)(e % N);
-    const double d = fabs(W[(long long)r * N + r]);
-    Tb[(long long)r * N + perm[c]] = (c >= r) ? W[(long long)c * N + r] / d : 0.0;
+  for (int e = tid; e < (int)NN; e += kThreads) {
+    const int r = e / N, c = e - r * N;
+    const double d = fabs(W[r * N + r]);
+    Tb[r * N + perm[c]] = (c >= r) ? W[c * N + r] / d : 0.0;
   }
   // Q = H_0 H_1 ... H_{N-1} by backward accumulation (column-major)
-  for (long long e = tid; e < NN; e += kThreads) {
-    const int c = (int)(e / N), r = (int)(e % N);
+  for (int e = tid; e < (int)NN; e += kThreads) {
+    const int c = e / N, r = e - c * N;
     Q[e] = (r == c) ? 1.0 : 0.0;
   }
   __syncthreads();
@@ -214,9 +214,9 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
     __syncthreads();
   }
   double* Ub = U + (long long)b * NN;
-  for (long long e = tid; e < NN; e += kThreads) {
-    const int r = (int)(e / N), c = (int)(e % N);
-    Ub[e] = Q[(long long)c * N + r];
+  for (int e = tid; e < (int)NN; e += kThreads) {
+    const int r = e / N, c = e - r * N;
+    Ub[e] = Q[c * N + r];
   }
 }
 
@@ -234,11 +234,11 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
   const double* Xb = X + (long long)b * NN;
   const double* Ub = UR + (long long)b * sUR;
   const double* Dv = DR + (long long)b * sDR;
-  for (long long e = tid; e < 2 * NN; e += kThreads) {
-    const int r = (int)(e / ld), c = (int)(e % ld);
+  for (int e = tid; e < 2 * (int)NN; e += kThreads) {
+    const int r = e / ld, c = e - r * ld;
     double v;
-    if (c < N) v = Xb[(long long)r * N + c];
-    else v = Ub[(long long)(c - N) * N + r] / fmax(Dv[r], 1.0);  // (Db_R^{-1} U_R^T)[r][c-N]
+    if (c < N) v = Xb[r * N + c];
+    else v = Ub[(c - N) * N + r] / fmax(Dv[r], 1.0);  // (Db_R^{-1} U_R^T)[r][c-N]
     Aug[e] = v;
   }
   __syncthreads();
@@ -263,22 +263,21 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
       }
       __syncthreads();
     }
-    const double inv = 1.0 / Aug[(long long)p * ld + p];
-    for (int c = p + 1 + tid; c < ld; c += kThreads) Aug[(long long)p * ld + c] *= inv;
+    const double inv = 1.0 / Aug[p * ld + p];
+    for (int c = p + 1 + tid; c < ld; c += kThreads) Aug[p * ld + c] *= inv;
     __syncthreads();
-    const int width = ld - p - 1;
-    for (long long e = tid; e < (long long)N * width; e += kThreads) {
-      const int r = (int)(e / width);
+    // rows over warps, columns over lanes (32-bit indices)
+    for (int r = warp; r < N; r += kWarps) {
       if (r == p) continue;
-      const int c = p + 1 + (int)(e % width);
-      Aug[(long long)r * ld + c] -= Aug[(long long)r * ld + p] * Aug[(long long)p * ld + c];
+      const double mlt = Aug[r * ld + p];
+      for (int c = p + 1 + lane; c < ld; c += 32) Aug[r * ld + c] -= mlt * Aug[p * ld + c];
     }
     __syncthreads();
   }
   double* Yb = Y + (long long)b * NN;
-  for (long long e = tid; e < NN; e += kThreads) {
-    const int r = (int)(e / N), c = (int)(e % N);
-    Yb[e] = Aug[(long long)r * ld + N + c];
+  for (int e = tid; e < (int)NN; e += kThreads) {
+    const int r = e / N, c = e - r * N;
+    Yb[e] = Aug[r * ld + N + c];
   }
 }
 
