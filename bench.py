@@ -29,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2106_00712_gb300.workloads import SQUARE_8x8 as WL  # noqa: E402
+from paper_2106_00712_gb300.sharding import weak_offset  # noqa: E402
 
 METRIC = "DQMC flips/s at |ΔG|≤1e-5 vs FP64, mixed vs FP64 path; serve p50/p99 latency"
 UNIT = "flips/s"
@@ -168,7 +169,7 @@ def run_path(nmc, torch, prec_name, steps, warmup, rank, stream, flush_buf):
     prec = PRECISIONS[prec_name]
     c = nmc.Context(WL.Lx, WL.Ly, WL.t, WL.U, WL.beta, WL.dtau, WL.n_wrap, seed=WL.seed,
                     n_chains=WL.n_chains, delay_k=WL.delay_k, precision=prec,
-                    drift_tol=1e300, chain_offset=rank * WL.n_chains,
+                    drift_tol=1e300, chain_offset=weak_offset(rank, WL.n_chains),
                     stream=stream.cuda_stream)
     try:
         c.generate()
@@ -202,7 +203,7 @@ def run_e2e(nmc, torch, prec_name, steps, rank, stream):
     fields = random_fields(WL.n_chains, WL.L_tau, WL.N, seed=1000 + rank)
     c = nmc.Context(WL.Lx, WL.Ly, WL.t, WL.U, WL.beta, WL.dtau, WL.n_wrap, seed=WL.seed,
                     n_chains=WL.n_chains, delay_k=WL.delay_k, precision=prec,
-                    drift_tol=1e300, chain_offset=rank * WL.n_chains,
+                    drift_tol=1e300, chain_offset=weak_offset(rank, WL.n_chains),
                     stream=stream.cuda_stream)
     try:
         c.set_fields(fields)                          # warm the path once
