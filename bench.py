@@ -162,7 +162,7 @@ def oracle_rate(cores, steps, warmup):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp32x2": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32x2": 2, "fp64_ph": 0, "fp32x2_ph": 2}
 
 
 def run_path(nmc, torch, prec_name, steps, warmup, rank, stream, flush_buf):
@@ -170,7 +170,7 @@ def run_path(nmc, torch, prec_name, steps, warmup, rank, stream, flush_buf):
     c = nmc.Context(WL.Lx, WL.Ly, WL.t, WL.U, WL.beta, WL.dtau, WL.n_wrap, seed=WL.seed,
                     n_chains=WL.n_chains, delay_k=WL.delay_k, precision=prec,
                     drift_tol=1e300, chain_offset=weak_offset(rank, WL.n_chains),
-                    stream=stream.cuda_stream)
+                    stream=stream.cuda_stream, ph_symmetric=prec_name.endswith("_ph"))
     try:
         c.generate()
         c.sweep(warmup, measure=1)
@@ -194,7 +194,7 @@ def run_path(nmc, torch, prec_name, steps, warmup, rank, stream, flush_buf):
     return ms, stats, obs
 
 
-def run_e2e(nmc, torch, prec_name, steps, rank, stream):
+def run_e2e(nmc, torch, prec_name, steps, rank, stream):  # noqa: C901
     """Same metric through the public C ABI with host buffers: host fields in, K measuring
     sweeps, observables and fields back to host, all inside the timed region."""
     import numpy as np
@@ -204,7 +204,7 @@ def run_e2e(nmc, torch, prec_name, steps, rank, stream):
     c = nmc.Context(WL.Lx, WL.Ly, WL.t, WL.U, WL.beta, WL.dtau, WL.n_wrap, seed=WL.seed,
                     n_chains=WL.n_chains, delay_k=WL.delay_k, precision=prec,
                     drift_tol=1e300, chain_offset=weak_offset(rank, WL.n_chains),
-                    stream=stream.cuda_stream)
+                    stream=stream.cuda_stream, ph_symmetric=prec_name.endswith("_ph"))
     try:
         c.set_fields(fields)                          # warm the path once
         c.sweep(1, measure=1)
@@ -233,7 +233,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", default="fp64,fp32x2,fp32")
+    ap.add_argument("--paths", default="fp64,fp32x2,fp32,fp64_ph,fp32x2_ph")
+    ap.add_argument("--value-paths", default="fp64,fp32x2,fp32",
+                    help="paths eligible for `value` (the per-spin G of the specification)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -299,29 +301,32 @@ def main():
                           "value": world * flips_per_step * args.steps / (ms_max * 1e-3)}
     clk = clocks.summary()
 
-    ok = [p for p in paths if results[p]["drift"] <= DRIFT_BAR]
-    best = max(ok or paths, key=lambda p: results[p]["value"])
+    eligible = [p for p in paths if p in args.value_paths.split(",")] or paths
+    ok = [p for p in eligible if results[p]["drift"] <= DRIFT_BAR]
+    best = max(ok or eligible, key=lambda p: results[p]["value"])
     r = results[best]
     st = r["stats"]
     dom = max(st, key=lambda k: st[k][2])          # kernel class with most device time
     launches_total = sum(v[0] for v in st.values())
-    per_launch_flop = 2.0 * WL.N ** 3 * 2 * WL.n_chains   # batched N x N x N, 2 per chain
+    ns = 1 if best.endswith("_ph") else 2
+    base = best[:-3] if best.endswith("_ph") else best
+    per_launch_flop = 2.0 * WL.N ** 3 * ns * WL.n_chains  # batched N x N x N, ns per chain
     # the dominant GEMM class of the chosen path and the peak of the pipe it runs on
-    gcls = "gemm_df" if best == "fp32x2" else "gemm"
+    gcls = "gemm_df" if base == "fp32x2" else "gemm"
     g_launch, g_timed, g_ms = st[gcls]
     achieved = per_launch_flop / (g_ms / max(g_timed, 1) * 1e-3) / 1e12
-    peak = PEAK_TFLOPS[best]
+    peak = PEAK_TFLOPS[base]
     traffic = None
     key = f"{gcls}_{best}"
     src = "gemm_df.cu" if gcls == "gemm_df" else "gemm.cu"
     if key in TRAFFIC and TRAFFIC[key]["src"] == src_hash(src):
         traffic = TRAFFIC[key]["bytes"]
     kname = {"fp64": "k_gemm<double,64>", "fp32": "k_gemm<float,64>",
-             "fp32x2": "k_gemm_df<64,64> (compensated FP32 pairs)"}[best]
+             "fp32x2": "k_gemm_df<64,64> (compensated FP32 pairs)"}[base]
     tot_ms = max(sum(x[2] for x in st.values()), 1e-30)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": PEAK_SOURCE[best], "dominant_class": dom,
+                "peak_source": PEAK_SOURCE[base], "dominant_class": dom,
                 "share": {k: v[2] / tot_ms for k, v in st.items() if v[0]}}
 
     e2e_dt, h2d, d2h, _ = run_e2e(nmc, torch, best, args.steps, rank, stream)
@@ -350,7 +355,7 @@ def main():
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32+f64", "fp32x2": "f32x2+f64"}[best],
+            "dtype": {"fp64": "f64", "fp32": "f32+f64", "fp32x2": "f32x2+f64"}[base],
             "data": "synthetic",
             "config": {**config, "path": best}, "paths": paths_out,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

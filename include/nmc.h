@@ -66,6 +66,10 @@ typedef struct {
                             <= 0 selects 1e-6 (FP64), 1e-3 (FP32), 1e-5 (FP32X2) default 0 */
   long long chain_offset;/* global index of local chain 0 (Philox counter word 2) def. 0   */
   void* cuda_stream;     /* cudaStream_t for all device work                     def. NULL */
+  int ph_symmetric;      /* 1: propagate spin up only; at half filling on the bipartite
+                            lattice G_dn = I - P G_up^T P (P = diag((-1)^{x+y})) exactly,
+                            R_dn = 1 + Delta_dn G_up_ii, and G~_dn follows the same way.
+                            Same chain, half the work.                           default 0  */
 } nmc_options;
 
 typedef struct {

@@ -23,13 +23,14 @@ constexpr int kThreads = 256;
 // Thread t owns column c = t % N of rows t / N, t / N + rows_per_pass, ... of both spins:
 // 32-bit index arithmetic only, consecutive threads on consecutive columns.
 template <typename T>
-__device__ void flush(T* G, const T* Ap, const T* Bp, int m, int N, int KK, long long NN) {
+__device__ void flush(T* G, const T* Ap, const T* Bp, int m, int N, int KK, long long NN,
+                      int ns) {
   // G[sp][r][c] += sum_{q<m} A[sp][q][r] * B[sp][q][c]
   const int nthr = blockDim.x;
   if ((int)threadIdx.x >= (nthr / N) * N && nthr >= N) return;
   const int c0 = threadIdx.x % N, r0 = threadIdx.x / N;
   const int rstep = nthr >= N ? nthr / N : 1;
-  for (int sp = 0; sp < 2; ++sp) {
+  for (int sp = 0; sp < ns; ++sp) {
     const T* A_ = Ap + sp * KK * N;
     const T* B_ = Bp + sp * KK * N;
     T* Gs = G + sp * NN;
@@ -54,14 +55,15 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
   const int c = blockIdx.x;
   const int N = f.N, KK = f.kk;
   const long long NN = (long long)N * N;
-  T* Ap = (T*)smraw;                // [2][KK][N]
-  T* Bp = Ap + 2 * KK * N;          // [2][KK][N]
-  T* diag = Bp + 2 * KK * N;        // [2][N]
-  T* Gs = diag + 2 * N;             // [2][N][N] when g_in_smem
-  double* u = (double*)(((uintptr_t)(Gs + (f.g_in_smem ? 2 * NN : 0)) + 15) & ~(uintptr_t)15);
+  const int ns = f.ns;
+  T* Ap = (T*)smraw;                // [ns][KK][N]
+  T* Bp = Ap + ns * KK * N;         // [ns][KK][N]
+  T* diag = Bp + ns * KK * N;       // [ns][N]
+  T* Gs = diag + ns * N;            // [ns][N][N] when g_in_smem
+  double* u = (double*)(((uintptr_t)(Gs + (f.g_in_smem ? ns * NN : 0)) + 15) & ~(uintptr_t)15);
   int8_t* sl = (int8_t*)(u + N);
 
-  T* Gg = f.G + (long long)c * 2 * NN;
+  T* Gg = f.G + (long long)c * ns * NN;
   T* G = f.g_in_smem ? Gs : Gg;
   int8_t* fl = f.fields + ((long long)c * f.L + f.l) * N;
   const uint32_t gchain = (uint32_t)(f.chain_offset + c);
@@ -74,13 +76,13 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
     u[i] = (double)ctr[0] * 2.3283064365386962890625e-10;  // 2^-32
   }
   if (f.g_in_smem)
-    for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) Gs[e] = Gg[e];
+    for (long long e = threadIdx.x; e < ns * NN; e += blockDim.x) Gs[e] = Gg[e];
   if (threadIdx.x == 0) {
     s_sign = f.sign[c];
     s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+  for (int i = threadIdx.x; i < ns * N; i += blockDim.x) {
     const int sp = i / N, r = i % N;
     diag[i] = G[sp * NN + (long long)r * N + r];
   }
@@ -93,18 +95,19 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
       const T* A_ = Ap + sp * KK * N;
       const T* B_ = Bp + sp * KK * N;
       T sum = T(0);
-      for (int q = q0; q < m; q += 16) sum = fma(A_[q * N + i], B_[q * N + i], sum);
+      if (sp < ns)
+        for (int q = q0; q < m; q += 16) sum = fma(A_[q * N + i], B_[q * N + i], sum);
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
       const T sum_dn = __shfl_sync(0xffffffffu, sum, 16);
       if (lane == 0) {
         const double gu = (double)(diag[i] + sum);
-        const double gd = (double)(diag[N + i] + sum_dn);
         const int s = sl[i];
         const double du = (s > 0) ? f.dm : f.dp;  // e^{-2 lam s} - 1
         const double dd = (s > 0) ? f.dp : f.dm;  // e^{+2 lam s} - 1
         const double Ru = 1.0 + du * (1.0 - gu);
-        const double Rd = 1.0 + dd * (1.0 - gd);
+        // spin down: 1 - G^dn_ii, or G^up_ii when G_dn = I - P G_up^T P
+        const double Rd = 1.0 + dd * (ns == 2 ? 1.0 - (double)(diag[N + i] + sum_dn) : gu);
         const double R = Ru * Rd;
         const bool mine = u[i] < fabs(R);
         bool acc = mine;
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
     __syncthreads();
     if (s_accept) {
       const T coef[2] = {(T)s_coef[0], (T)s_coef[1]};
-      for (int t = threadIdx.x; t < 4 * N; t += blockDim.x) {
+      for (int t = threadIdx.x; t < 2 * ns * N; t += blockDim.x) {
         const int sp = t / (2 * N);
         const int kind = (t / N) & 1;
         const int r = t % N;
@@ -146,10 +149,10 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
       ++m;
       __syncthreads();
       if (m == KK) {
-        flush(G, Ap, Bp, m, N, KK, NN);
+        flush(G, Ap, Bp, m, N, KK, NN, f.ns);
         m = 0;
         __syncthreads();
-        for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) {
+        for (int j = threadIdx.x; j < ns * N; j += blockDim.x) {
           const int sp = j / N, r = j % N;
           diag[j] = G[sp * NN + (long long)r * N + r];
         }
@@ -158,11 +161,11 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
     }
   }
   if (m > 0) {
-    flush(G, Ap, Bp, m, N, KK, NN);
+    flush(G, Ap, Bp, m, N, KK, NN, f.ns);
     __syncthreads();
   }
   if (f.g_in_smem)
-    for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) Gg[e] = Gs[e];
+    for (long long e = threadIdx.x; e < ns * NN; e += blockDim.x) Gg[e] = Gs[e];
   for (int i = threadIdx.x; i < N; i += blockDim.x) fl[i] = sl[i];
   if (threadIdx.x == 0) {
     f.sign[c] = s_sign;
@@ -181,12 +184,12 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
 // G^_ii -- both give the FP64 decision. The update coefficient -Delta/R^sigma uses a
 // double-float reciprocal.
 __device__ void flush_df(df2* G, const df2* Ap, const df2* Bp, int m, int N, int KK,
-                         long long NN) {
+                         long long NN, int ns) {
   const int nthr = blockDim.x;
   if ((int)threadIdx.x >= (nthr / N) * N && nthr >= N) return;
   const int c0 = threadIdx.x % N, r0 = threadIdx.x / N;
   const int rstep = nthr >= N ? nthr / N : 1;
-  for (int sp = 0; sp < 2; ++sp) {
+  for (int sp = 0; sp < ns; ++sp) {
     const df2* A_ = Ap + sp * KK * N;
     const df2* B_ = Bp + sp * KK * N;
     df2* Gs = G + sp * NN;
@@ -210,16 +213,17 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
   const int c = blockIdx.x;
   const int N = f.N, KK = f.kk;
   const long long NN = (long long)N * N;
+  const int ns = f.ns;
   df2* Ap = (df2*)smraw;
-  df2* Bp = Ap + 2 * KK * N;
-  df2* dg = Bp + 2 * KK * N;          // running diagonal of G^, [2][N]
-  df2* Gs = dg + 2 * N;
+  df2* Bp = Ap + ns * KK * N;
+  df2* dg = Bp + ns * KK * N;         // running diagonal of G^, [ns][N]
+  df2* Gs = dg + ns * N;
   // uniforms as FP32 pairs: u = x0 * 2^-32 has at most 32 significant bits, so the pair
   // holds it exactly
-  df2* udf = (df2*)(((uintptr_t)(Gs + (f.g_in_smem ? 2 * NN : 0)) + 15) & ~(uintptr_t)15);
+  df2* udf = (df2*)(((uintptr_t)(Gs + (f.g_in_smem ? ns * NN : 0)) + 15) & ~(uintptr_t)15);
   int8_t* sl = (int8_t*)(udf + N);
 
-  df2* Gg = f.G + (long long)c * 2 * NN;
+  df2* Gg = f.G + (long long)c * ns * NN;
   df2* G = f.g_in_smem ? Gs : Gg;
   int8_t* fl = f.fields + ((long long)c * f.L + f.l) * N;
   const uint32_t gchain = (uint32_t)(f.chain_offset + c);
@@ -232,13 +236,13 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
     udf[i] = df_from_double((double)ctr[0] * 2.3283064365386962890625e-10);  // 2^-32
   }
   if (f.g_in_smem)
-    for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) Gs[e] = Gg[e];
+    for (long long e = threadIdx.x; e < ns * NN; e += blockDim.x) Gs[e] = Gg[e];
   if (threadIdx.x == 0) {
     s_sign = f.sign[c];
     s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) {
+  for (int i = threadIdx.x; i < ns * N; i += blockDim.x) {
     const int sp = i / N, r = i % N;
     dg[i] = G[sp * NN + (long long)r * N + r];
   }
@@ -249,11 +253,13 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
   for (int i = 0; i < N; ++i) {
     if (threadIdx.x == 0) {
       const int s = sl[i];
-      const df2 gu = dg[i], gd = dg[N + i];
+      const df2 gu = dg[i];
       const df2 du = (s > 0) ? f.dm2 : f.dp2;  // e^{-2 lam s} - 1
       const df2 dd = (s > 0) ? f.dp2 : f.dm2;  // e^{+2 lam s} - 1
       const df2 Ru = df_add(one, df_mul(du, df_add(one, df_neg(gu))));
-      const df2 Rd = df_add(one, df_mul(dd, df_add(one, df_neg(gd))));
+      // spin down: 1 - G^dn_ii, or G^up_ii when G_dn = I - P G_up^T P
+      const df2 omd = ns == 2 ? df_add(one, df_neg(dg[N + i])) : gu;
+      const df2 Rd = df_add(one, df_mul(dd, omd));
       const df2 R = df_mul(Ru, Rd);
       const df2 diff = df_add(udf[i], df_neg(df_abs(R)));
       const float margin = 1e-10f * (fabsf(R.hi) + 1.f);
@@ -262,9 +268,10 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
       if (fabsf(diff.hi) > margin) {
         mine = diff.hi < 0.f;
       } else {  // certified FP64 evaluation from the same G^_ii
-        const double g64u = df_to_double(gu), g64d = df_to_double(gd);
+        const double g64u = df_to_double(gu);
+        const double omd64 = ns == 2 ? 1.0 - df_to_double(dg[N + i]) : g64u;
         const double d64u = (s > 0) ? f.dm : f.dp, d64d = (s > 0) ? f.dp : f.dm;
-        const double R64 = (1.0 + d64u * (1.0 - g64u)) * (1.0 + d64d * (1.0 - g64d));
+        const double R64 = (1.0 + d64u * (1.0 - g64u)) * (1.0 + d64d * omd64);
         mine = df_to_double(udf[i]) < fabs(R64);
         Rsign = R64;
       }
@@ -285,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
     }
     __syncthreads();
     if (s_accept) {
-      for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+      for (int t = threadIdx.x; t < ns * N; t += blockDim.x) {
         const int sp = t / N, r = t % N;
         const df2* Gsp = G + sp * NN;
         const df2* A_ = Ap + sp * KK * N;
@@ -307,10 +314,10 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
       ++m;
       __syncthreads();
       if (m == KK) {
-        flush_df(G, Ap, Bp, m, N, KK, NN);
+        flush_df(G, Ap, Bp, m, N, KK, NN, f.ns);
         m = 0;
         __syncthreads();
-        for (int j = threadIdx.x; j < 2 * N; j += blockDim.x) {
+        for (int j = threadIdx.x; j < ns * N; j += blockDim.x) {
           const int sp = j / N, r = j % N;
           dg[j] = G[sp * NN + (long long)r * N + r];
         }
@@ -319,11 +326,11 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
     }
   }
   if (m > 0) {
-    flush_df(G, Ap, Bp, m, N, KK, NN);
+    flush_df(G, Ap, Bp, m, N, KK, NN, f.ns);
     __syncthreads();
   }
   if (f.g_in_smem)
-    for (long long e = threadIdx.x; e < 2 * NN; e += blockDim.x) Gg[e] = Gs[e];
+    for (long long e = threadIdx.x; e < ns * NN; e += blockDim.x) Gg[e] = Gs[e];
   for (int i = threadIdx.x; i < N; i += blockDim.x) fl[i] = sl[i];
   if (threadIdx.x == 0) {
     f.sign[c] = s_sign;
@@ -335,9 +342,9 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
 
 }  // namespace
 
-size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem) {
-  size_t b = (size_t)(4 * kk * N + 2 * N) * elem;
-  if (g_in_smem) b += 2 * (size_t)N * N * elem;
+size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem, int ns) {
+  size_t b = (size_t)(2 * ns * kk * N + ns * N) * elem;
+  if (g_in_smem) b += (size_t)ns * N * N * elem;
   b = (b + 15) & ~(size_t)15;
   b += (size_t)N * sizeof(double) + (size_t)N + 16;
   return b;
@@ -345,7 +352,7 @@ size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem) {
 
 template <typename T>
 void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st) {
-  const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(T), f.g_in_smem);
+  const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(T), f.g_in_smem, f.ns);
   cudaFuncSetAttribute(k_flip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_flip<T><<<n_chains, kThreads, bytes, st>>>(f);
 }
@@ -355,7 +362,7 @@ template void flip_slice<float>(const FlipArgs<float>&, int, cudaStream_t);
 
 template <>
 void flip_slice<df2>(const FlipArgs<df2>& f, int n_chains, cudaStream_t st) {
-  const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(df2), f.g_in_smem);
+  const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(df2), f.g_in_smem, f.ns);
   cudaFuncSetAttribute(k_flip_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   k_flip_df<<<n_chains, kThreads, bytes, st>>>(f);
 }

@@ -112,7 +112,7 @@ k_gemm(const GemmArgs<T> g) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dmax = nan_max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
     if ((tid & 31) == 0 && dmax != 0.0)
-      atomicMax(g.drift + (b >> 1), (unsigned long long)__double_as_longlong(dmax));
+      atomicMax(g.drift + (g.ns == 2 ? b >> 1 : b), (unsigned long long)__double_as_longlong(dmax));
   }
 }
 

@@ -12,10 +12,10 @@ namespace nmc {
 
 namespace {
 
-__device__ __forceinline__ int field_m(const int8_t* f, long long fstride, int b, int r, int c,
-                                       int kr, int kc) {
-  const int sg = (b & 1) ? -1 : 1;
-  const int8_t* fb = f + (long long)(b >> 1) * fstride;
+__device__ __forceinline__ int field_m(const int8_t* f, long long fstride, int ns, int b, int r,
+                                       int c, int kr, int kc) {
+  const int sg = (ns == 2 && (b & 1)) ? -1 : 1;
+  const int8_t* fb = f + (long long)(ns == 2 ? b >> 1 : b) * fstride;
   int m = 0;
   if (kr) m += kr * (fb[r] > 0 ? 1 : -1);
   if (kc) m += kc * (fb[c] > 0 ? 1 : -1);
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_df(const DfGemmA
       if (gk < g.K && gn < g.N) {
         v = B[(long long)gk * g.ldb + gn];
         if (bscale) {
-          const int m = field_m(g.bfields, g.fstride, b, gk, gn, g.br, g.bc);
+          const int m = field_m(g.bfields, g.fstride, g.ns, b, gk, gn, g.br, g.bc);
           if (m) v = df_mul(v, g.e[m + 2]);
         }
       }
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN)) k_gemm_df(const DfGemmA
       if (gn >= g.N) continue;
       df2 v = df_finish(acc[i][j]);
       if (g.cfields) {
-        const int m = field_m(g.cfields, g.fstride, b, gm, gn, g.cr, g.cc);
+        const int m = field_m(g.cfields, g.fstride, g.ns, b, gm, gn, g.cr, g.cc);
         if (m) v = df_mul(v, g.e[m + 2]);
       }
       const long long idx = (long long)b * g.sC + (long long)gm * g.ldc + gn;

@@ -80,27 +80,33 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 //  dens  = (1/N) sum_i (2 - G~up_ii - G~dn_ii)
 //  S     = (1/4N) [ (sum_i p_i m_i)^2 + sum_sigma sum_ij p_i p_j (delta_ij - G~_ji) G~_ij ],
 //          m_i = G~dn_ii - G~up_ii, p_i = (-1)^{x_i + y_i}
+// With ns = 1 only G~up is stored and G~dn_ij = delta_ij - p_i p_j G~up_ji.
 __global__ void __launch_bounds__(kMeasThreads)
 k_measure(const double* __restrict__ Gt, const double* __restrict__ K,
-          const double* __restrict__ sign, int Lx, int Ly, double U, double* __restrict__ acc) {
+          const double* __restrict__ sign, int Lx, int Ly, double U, int ns,
+          double* __restrict__ acc) {
   __shared__ double red[kMeasThreads / 32];
   const int c = blockIdx.x;
   const int N = Lx * Ly;
   const long long NN = (long long)N * N;
-  const double* Gu = Gt + (long long)c * 2 * NN;
-  const double* Gd = Gu + NN;
+  const double* Gu = Gt + (long long)c * ns * NN;
+  const double* Gd = Gu + NN;  // only read when ns == 2
   double kin = 0.0, conn = 0.0;
   for (int e = threadIdx.x; e < (int)NN; e += blockDim.x) {
     const int i = e / N, j = e - i * N;
     const int ji = j * N + i;
-    kin += K[e] * (Gu[ji] + Gd[ji]);
     const double pij = (((i % Lx) + (i / Lx) + (j % Lx) + (j / Lx)) & 1) ? -1.0 : 1.0;
     const double dij = (i == j) ? 1.0 : 0.0;
-    conn += pij * ((dij - Gu[ji]) * Gu[e] + (dij - Gd[ji]) * Gd[e]);
+    const double gu_ij = Gu[e], gu_ji = Gu[ji];
+    const double gd_ij = ns == 2 ? Gd[e] : dij - pij * gu_ji;
+    const double gd_ji = ns == 2 ? Gd[ji] : dij - pij * gu_ij;
+    kin += K[e] * (gu_ji + gd_ji);
+    conn += pij * ((dij - gu_ji) * gu_ij + (dij - gd_ji) * gd_ij);
   }
   double epot = 0.0, docc = 0.0, dens = 0.0, stag = 0.0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const double gu = Gu[(long long)i * N + i], gd = Gd[(long long)i * N + i];
+    const double gu = Gu[(long long)i * N + i];
+    const double gd = ns == 2 ? Gd[(long long)i * N + i] : 1.0 - gu;
     epot += (0.5 - gu) * (0.5 - gd);
     docc += (1.0 - gu) * (1.0 - gd);
     dens += 2.0 - gu - gd;
@@ -166,8 +172,8 @@ void philox_batch(const uint32_t* c0, int n, uint32_t c1, uint32_t c2, uint32_t 
 }
 
 void measure(const double* Gt, const double* K, const double* sign, int Lx, int Ly, double U,
-             double* acc, int n_chains, cudaStream_t st) {
-  k_measure<<<n_chains, kMeasThreads, 0, st>>>(Gt, K, sign, Lx, Ly, U, acc);
+             double* acc, int n_chains, int ns, cudaStream_t st) {
+  k_measure<<<n_chains, kMeasThreads, 0, st>>>(Gt, K, sign, Lx, Ly, U, ns, acc);
 }
 
 }  // namespace nmc

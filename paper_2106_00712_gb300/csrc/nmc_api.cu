@@ -100,7 +100,8 @@ struct nmc_ctx {
 
   cudaStream_t st() const { return (cudaStream_t)opt.cuda_stream; }
   int chains() const { return opt.n_chains; }
-  int batch() const { return 2 * opt.n_chains; }
+  int ns() const { return opt.ph_symmetric ? 1 : 2; }
+  int batch() const { return ns() * opt.n_chains; }
   long long NN() const { return (long long)N * N; }
   bool fp32() const { return opt.precision == NMC_FP32; }
   bool dfp() const { return opt.precision == NMC_FP32X2; }
@@ -293,8 +294,9 @@ void clamp_delay(nmc_ctx* x) {
   const size_t elem = x->fp32() ? sizeof(float) : sizeof(double);
   const size_t limit = 200 * 1024;
   int kk = std::max(1, std::min(x->opt.delay_k, x->N));
-  x->g_in_smem = flip_smem_bytes(x->N, kk, elem, 1) <= limit ? 1 : 0;
-  while (kk > 1 && flip_smem_bytes(x->N, kk, elem, x->g_in_smem) > limit) --kk;
+  const int ns = x->opt.ph_symmetric ? 1 : 2;
+  x->g_in_smem = flip_smem_bytes(x->N, kk, elem, 1, ns) <= limit ? 1 : 0;
+  while (kk > 1 && flip_smem_bytes(x->N, kk, elem, x->g_in_smem, ns) > limit) --kk;
   x->kk = kk;
 }
 
@@ -302,6 +304,7 @@ void clamp_delay(nmc_ctx* x) {
 ScaleDesc field_scale(const nmc_ctx* x, int l, bool inv) {
   ScaleDesc d;
   d.kind = inv ? SC_FIELD_INV : SC_FIELD;
+  d.ns = x->ns();
   d.fields = x->dS + (long long)l * x->N;
   d.fstride = (long long)x->Lt * x->N;
   d.e_lam = std::exp(x->lam);
@@ -326,6 +329,7 @@ GemmArgs<T> gemm_base(const nmc_ctx* x, const T* A, long long sA, const T* B, lo
   g.A = A; g.sA = sA; g.lda = x->N;
   g.B = B; g.sB = sB; g.ldb = x->N;
   g.C = C; g.sC = x->NN(); g.ldc = x->N;
+  g.ns = x->ns();
   return g;
 }
 
@@ -337,6 +341,7 @@ DfGemmArgs df_base(const nmc_ctx* x, const df2* A, long long sA, const df2* B, l
   g.B = B; g.sB = sB; g.ldb = x->N;
   g.sC = x->NN(); g.ldc = x->N;
   g.fstride = (long long)x->Lt * x->N;
+  g.ns = x->ns();
   for (int m = -2; m <= 2; ++m) {
     const double v = std::exp(m * x->lam);
     const float hi = (float)v;
@@ -419,17 +424,17 @@ void flip(nmc_ctx* x, int l, const uint8_t* replay) {
     };
     FlipArgs<df2> f{x->dG2, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                     (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
-                    x->dCounts, replay, nullptr, split(dm), split(dp)};
+                    x->dCounts, replay, nullptr, split(dm), split(dp), x->ns()};
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   } else if (x->fp32()) {
     FlipArgs<float> f{x->dGf, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                       (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
-                      x->dCounts, replay, nullptr};
+                      x->dCounts, replay, nullptr, df2{0.f, 0.f}, df2{0.f, 0.f}, x->ns()};
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   } else {
     FlipArgs<double> f{x->dG, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                        (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
-                       x->dCounts, replay, nullptr};
+                       x->dCounts, replay, nullptr, df2{0.f, 0.f}, df2{0.f, 0.f}, x->ns()};
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   }
 }
@@ -543,12 +548,12 @@ void measure_now(nmc_ctx* x) {
     DfGemmArgs h = df_base(x, x->dT12, NN, x->dEmh2, 0);
     h.Cd = x->dM1;
     launch(x, KC_GEMM_DF, [&] { gemm_df(h, st); });
-    launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), st); });
+    launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), x->ns(), st); });
     return;
   }
   launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dEph, 0, x->dG, NN, x->dT1), st); });   // e^{dtau K/2} G
   launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dT1, NN, x->dEmh, 0, x->dM1), st); });  // ... e^{-dtau K/2}
-  launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), st); });
+  launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), x->ns(), st); });
 }
 
 void sweep_up(nmc_ctx* x, bool meas, const uint8_t* replay) {
@@ -726,6 +731,7 @@ void nmc_default_options(nmc_options* o) {
   o->drift_tol = 0.0;
   o->chain_offset = 0;
   o->cuda_stream = nullptr;
+  o->ph_symmetric = 0;
 }
 
 nmc_status nmc_create(int Lx, int Ly, double t, double U, double beta, double dtau, int n_wrap,
@@ -765,7 +771,7 @@ nmc_status nmc_configure(nmc_ctx* x, const nmc_options* o) {
   nmc_default_options(&n);
   if (o) n = *o;
   if (n.n_chains < 1 || n.delay_k < 1 || (n.precision != NMC_FP64 && n.precision != NMC_FP32 && n.precision != NMC_FP32X2) ||
-      n.chain_offset < 0 || n.n_chains > (1 << 20))
+      n.chain_offset < 0 || n.n_chains > (1 << 20) || (n.ph_symmetric != 0 && n.ph_symmetric != 1))
     return fail(x, NMC_EINVAL, "invalid nmc_options");
   x->opt = n;
   clamp_delay(x);
@@ -931,7 +937,8 @@ nmc_status nmc_get_green(nmc_ctx* x, int chain, int spin, double* G) {
   if (!x->have_fields) return fail(x, NMC_ESTATE, "no fields set");
   NMC_CUDA(x, cudaSetDevice(x->device));
   const long long NN = x->NN();
-  const long long off = ((long long)chain * 2 + spin) * NN;
+  const int sp_stored = x->ns() == 2 ? spin : 0;
+  const long long off = ((long long)chain * x->ns() + sp_stored) * NN;
   if (x->dfp()) {
     std::vector<df2> tmp(NN);
     NMC_CUDA(x, cudaMemcpyAsync(tmp.data(), x->dG2 + off, NN * sizeof(df2),
@@ -948,6 +955,15 @@ nmc_status nmc_get_green(nmc_ctx* x, int chain, int spin, double* G) {
     NMC_CUDA(x, cudaMemcpyAsync(G, x->dG + off, NN * sizeof(double), cudaMemcpyDeviceToHost,
                                 x->st()));
     NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  }
+  if (x->ns() == 1 && spin == 1) {  // G_dn = I - P G_up^T P, p_i = (-1)^{x_i + y_i}
+    const int N = x->N;
+    std::vector<double> up(G, G + NN);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        const int pij = (((i % x->Lx) + (i / x->Lx) + (j % x->Lx) + (j / x->Lx)) & 1) ? -1 : 1;
+        G[(size_t)i * N + j] = (i == j ? 1.0 : 0.0) - pij * up[(size_t)j * N + i];
+      }
   }
   return NMC_OK;
 }
@@ -977,7 +993,7 @@ nmc_status nmc_checkpoint(nmc_ctx* x, void* buf, size_t* n) {
   NMC_CUDA(x, cudaSetDevice(x->device));
   char* p = (char*)buf;
   const int64_t h[9] = {(int64_t)kCkptMagic, x->N, x->Lt, C, (int64_t)x->seed, x->sweep_counter,
-                        x->phase, x->n_series, x->opt.precision};
+                        x->phase, x->n_series, x->opt.precision + 16 * x->opt.ph_symmetric};
   std::memcpy(p, h, hdr);
   p += hdr;
   cudaStream_t st = x->st();
@@ -1003,7 +1019,7 @@ nmc_status nmc_restore(nmc_ctx* x, const void* buf, size_t n) {
   std::memcpy(h, buf, hdr);
   const int C = x->opt.n_chains;
   if ((uint64_t)h[0] != kCkptMagic || h[1] != x->N || h[2] != x->Lt || h[3] != C ||
-      (uint64_t)h[4] != x->seed || h[8] != x->opt.precision)
+      (uint64_t)h[4] != x->seed || h[8] != x->opt.precision + 16 * x->opt.ph_symmetric)
     return fail(x, NMC_EINVAL, "nmc_restore: checkpoint does not match this context");
   const size_t nf = (size_t)C * x->Lt * x->N;
   const long long ns = h[7];

@@ -44,6 +44,7 @@ enum ScaleKind : int {
 
 struct ScaleDesc {
   int kind = SC_NONE;
+  int ns = 2;                      // spins per chain in the batch (2, or 1 = spin up only)
   const double* vec = nullptr;   // SC_VEC/INV_MAX1/MIN1: v + b*vstride
   long long vstride = 0;
   const int8_t* fields = nullptr;  // SC_FIELD*: fields + chain*fstride (already + l*N)
@@ -58,8 +59,8 @@ __device__ __forceinline__ double scale_at(const ScaleDesc& d, int b, int i) {
     case SC_MIN1: return fmin(d.vec[b * d.vstride + i], 1.0);
     case SC_FIELD:
     case SC_FIELD_INV: {
-      const int s = d.fields[(long long)(b >> 1) * d.fstride + i];
-      const bool up = (b & 1) == 0;
+      const int s = d.fields[(long long)(d.ns == 2 ? b >> 1 : b) * d.fstride + i];
+      const bool up = d.ns == 1 || (b & 1) == 0;
       bool pos = (s > 0) == up;          // sigma * s > 0
       if (d.kind == SC_FIELD_INV) pos = !pos;
       return pos ? d.e_lam : d.e_mlam;
@@ -85,6 +86,7 @@ struct GemmArgs {
   long long sRef = 0;                               // (ref_is_float: 1 = float, 2 = df2)
   unsigned long long* drift = nullptr;              // per chain: bits of max |C - ref|
   df2* Cdf = nullptr; long long sCdf = 0;           // double-float copy, ld = ldc
+  int ns = 2;                                       // spins per chain (drift index)
 };
 
 void gemm(const GemmArgs<double>& g, cudaStream_t st);
@@ -104,7 +106,8 @@ struct DfGemmArgs {
   const int8_t* bfields = nullptr; int br = 0, bc = 0;
   const int8_t* cfields = nullptr; int cr = 0, cc = 0;
   long long fstride = 0;
-  df2 e[5];  // e^{m lam}, m = -2..2
+  int ns = 2;  // spins per chain in the batch
+  df2 e[5];    // e^{m lam}, m = -2..2
 };
 void gemm_df(const DfGemmArgs& g, cudaStream_t st);
 void split_to_df(const double* x, df2* y, long long n, cudaStream_t st);
@@ -136,9 +139,10 @@ struct FlipArgs {
   const uint8_t* replay;     // [chain][L][N] or null
   T* panels_g;               // unused (panels live in shared memory)
   df2 dm2, dp2;              // dm, dp as FP32 pairs (compensated mode)
+  int ns;                    // 2 spins, or 1: spin up only, G_dn = I - P G_up^T P
 };
 template <typename T> void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st);
-size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem);
+size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem, int ns);
 
 // ---------------------------------------------------------------------------- misc
 void init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0, uint32_t k1,
@@ -153,7 +157,8 @@ void philox_batch(const uint32_t* c0, int n, uint32_t c1, uint32_t c2, uint32_t 
 // Measurement on Gt = e^{dtau K/2} G e^{-dtau K/2}: adds per-chain sums of
 // (energy, ekin, double_occ, s_pipi, density) * sign and sign into acc[chain][8].
 constexpr int kNumObs = 6;   // energy, ekin, docc, s_pipi, density, sign
+// ns = 1: only G~up is given and G~dn = I - P G~up^T P (particle-hole symmetry).
 void measure(const double* Gt, const double* K, const double* sign, int Lx, int Ly, double U,
-             double* acc, int n_chains, cudaStream_t st);
+             double* acc, int n_chains, int ns, cudaStream_t st);
 
 }  // namespace nmc

@@ -40,12 +40,12 @@ def _ctx(nmc, model, **kw):
 
 
 def _compare_run(nmc, model, chains, n_sweeps, measure_from=0, delay_k=16, fields=None,
-                 check_chains=None, chain_offset=0, precision=0, g_rel=G_REL):
+                 check_chains=None, chain_offset=0, precision=0, g_rel=G_REL, ph=0):
     """Run n_sweeps on the GPU and on the oracle for the checked chains; compare the
     field after every sweep (bit-exact), G at the end and the accumulated observables."""
     check = list(range(chains)) if check_chains is None else check_chains
     with _ctx(nmc, model, n_chains=chains, delay_k=delay_k, chain_offset=chain_offset,
-              drift_tol=1e-3, precision=precision) as c:
+              drift_tol=1e-3, precision=precision, ph_symmetric=ph) as c:
         if fields is None:
             c.generate()
             refs = {ch: Chain(model, initial_fields(model, ch + chain_offset), ch + chain_offset)
@@ -276,6 +276,29 @@ def test_fp32x2_8x8_256_chains_sampled(nmc):
     model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=0)
     _compare_run(nmc, model, chains=256, n_sweeps=2, measure_from=0, delay_k=16,
                  check_chains=[3, 200], precision=nmc.NMC_FP32X2, g_rel=G_REL_X2)
+
+
+# particle-hole single-spin mode: spin down derived from spin up, same chain
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_ph_single_spin_4x4_matches_oracle(nmc, prec):
+    model = Model(4, 4, 1.0, 4.0, 2.0, 0.1, 10, seed=0)
+    _compare_run(nmc, model, chains=2, n_sweeps=40, measure_from=5, precision=prec,
+                 g_rel=G_REL if prec == 0 else G_REL_X2, ph=1)
+
+
+@pytest.mark.parametrize("Lx,Ly,n_wrap,k,prec", [
+    (2, 1, 2, 16, 0), (6, 6, 5, 5, 0), (10, 10, 5, 16, 2), (12, 12, 5, 8, 0)])
+def test_ph_single_spin_ragged_sizes(nmc, Lx, Ly, n_wrap, k, prec):
+    model = Model(Lx, Ly, 1.0, 4.0, 1.0, 0.1, n_wrap, seed=29)
+    _compare_run(nmc, model, chains=2, n_sweeps=3, measure_from=1, delay_k=k, precision=prec,
+                 g_rel=G_REL if prec == 0 else G_REL_X2, ph=1)
+
+
+def test_ph_single_spin_8x8_256_chains_sampled(nmc):
+    model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=0)
+    _compare_run(nmc, model, chains=256, n_sweeps=2, measure_from=0, delay_k=16,
+                 check_chains=[0, 255], precision=nmc.NMC_FP32X2, g_rel=G_REL_X2, ph=1)
 
 
 def test_state_errors_on_device(nmc):
