@@ -176,6 +176,11 @@ nmc_status nmc_philox_device(const uint32_t* d_c0, int n, uint32_t c1, uint32_t 
                              uint32_t c3, uint32_t k0, uint32_t k1, uint32_t* d_out,
                              void* cuda_stream);
 
+/* Drift history: out[k] = max over chains of max|G_propagated - G_recomputed| at the k-th
+ * stabilization since the fields were set (first `max` entries; the library keeps the
+ * first 4096). *n receives the number of stabilizations so far. Synchronises the stream. */
+nmc_status nmc_drift_history(nmc_ctx* ctx, double* out, long long max, long long* n);
+
 /* Per-kernel accounting (tracing). Every library kernel launch is counted by class
  * ("gemm", "flip", "qrp", "solve", "measure", "other", "gemm_df"). With profiling enabled, each
  * launch is also bracketed by CUDA events on the context stream, and nmc_kernel_stats

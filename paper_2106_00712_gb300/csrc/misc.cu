@@ -134,6 +134,26 @@ k_measure(const double* __restrict__ Gt, const double* __restrict__ K,
   }
 }
 
+// cumulative[c] = max(cumulative[c], stab[c]); hist = max_c stab[c] (one CTA)
+__global__ void k_fold_drift(const unsigned long long* stab, unsigned long long* cumulative,
+                             unsigned long long* hist, int n) {
+  __shared__ unsigned long long red[256];
+  unsigned long long m = 0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    const unsigned long long v = stab[c];
+    if (v > cumulative[c]) cumulative[c] = v;
+    if (v > m) m = v;
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o && red[threadIdx.x + o] > red[threadIdx.x])
+      red[threadIdx.x] = red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && hist) *hist = red[0];
+}
+
 int grid_for(long long n) {
   long long g = (n + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
@@ -169,6 +189,11 @@ void philox_batch(const uint32_t* c0, int n, uint32_t c1, uint32_t c2, uint32_t 
                   uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st) {
   if (n <= 0) return;
   k_philox<<<(n + 255) / 256, 256, 0, st>>>(c0, n, c1, c2, c3, k0, k1, out);
+}
+
+void fold_drift(const unsigned long long* stab, unsigned long long* cumulative,
+                unsigned long long* hist, int n_chains, cudaStream_t st) {
+  k_fold_drift<<<1, 256, 0, st>>>(stab, cumulative, hist, n_chains);
 }
 
 void measure(const double* Gt, const double* K, const double* sign, int Lx, int Ly, double U,

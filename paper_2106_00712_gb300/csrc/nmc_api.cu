@@ -84,6 +84,9 @@ struct nmc_ctx {
   double* dSign = nullptr;
   unsigned long long* dCounts = nullptr;  // [chain][3]: attempts, accepts, disagreements
   unsigned long long* dDrift = nullptr;   // [chain]: bits of max drift
+  unsigned long long* dDriftStab = nullptr;  // [chain]: drift of the current recompute
+  unsigned long long* dHist = nullptr;    // [stabilization]: max over chains
+  long long hist_cap = 0, n_hist = 0;
   double* dSeries = nullptr;              // [slot][chain][8]
   long long series_cap = 0, n_series = 0;
   uint8_t* dReplay = nullptr;
@@ -186,6 +189,9 @@ void free_all(nmc_ctx* x) {
   x->dSign = nullptr;
   x->dCounts = nullptr;
   x->dDrift = nullptr;
+  x->dDriftStab = nullptr;
+  x->dHist = nullptr;
+  x->hist_cap = x->n_hist = 0;
   x->dSeries = nullptr;
   x->series_cap = x->n_series = 0;
   x->dReplay = nullptr;
@@ -257,6 +263,9 @@ nmc_status alloc_all(nmc_ctx* x) {
   NMC_TRY(dalloc(x, &x->dSign, x->chains()));
   NMC_TRY(dalloc(x, &x->dCounts, 3 * (size_t)x->chains()));
   NMC_TRY(dalloc(x, &x->dDrift, x->chains()));
+  NMC_TRY(dalloc(x, &x->dDriftStab, x->chains()));
+  x->hist_cap = 4096;
+  NMC_TRY(dalloc(x, &x->dHist, x->hist_cap));
 
   cudaStream_t st = x->st();
   const size_t mb = NN * sizeof(double);
@@ -530,11 +539,18 @@ void recompute(nmc_ctx* x, const UDTView& R, const UDTView& L, bool drift) {
     g3.ref = x->fp32() ? (const void*)x->dGf : x->dfp() ? (const void*)x->dG2 : (const void*)x->dG;
     g3.ref_is_float = x->fp32() ? 1 : x->dfp() ? 2 : 0;
     g3.sRef = NN;
-    g3.drift = x->dDrift;
+    g3.drift = x->dDriftStab;
+    cudaMemsetAsync(x->dDriftStab, 0, sizeof(unsigned long long) * x->chains(), st);
   }
   if (x->fp32()) { g3.Cf = x->dGf; g3.sCf = NN; }
   if (x->dfp()) { g3.Cdf = x->dG2; g3.sCdf = NN; }
   launch(x, KC_GEMM, [&] { gemm(g3, st); });
+  if (drift) {
+    unsigned long long* hist =
+        x->n_hist < x->hist_cap ? x->dHist + x->n_hist : nullptr;
+    launch(x, KC_OTHER, [&] { fold_drift(x->dDriftStab, x->dDrift, hist, x->chains(), st); });
+    ++x->n_hist;
+  }
 }
 
 void measure_now(nmc_ctx* x) {
@@ -615,6 +631,8 @@ nmc_status reset_chain_state(nmc_ctx* x) {
                               cudaMemcpyHostToDevice, st));
   NMC_CUDA(x, cudaMemsetAsync(x->dCounts, 0, 3 * sizeof(unsigned long long) * x->chains(), st));
   NMC_CUDA(x, cudaMemsetAsync(x->dDrift, 0, sizeof(unsigned long long) * x->chains(), st));
+  NMC_CUDA(x, cudaMemsetAsync(x->dHist, 0, sizeof(unsigned long long) * x->hist_cap, st));
+  x->n_hist = 0;
   x->n_series = 0;
   x->phase = 0;
   NMC_CUDA(x, cudaStreamSynchronize(st));
@@ -1076,6 +1094,23 @@ nmc_status nmc_philox_device(const uint32_t* d_c0, int n, uint32_t c1, uint32_t 
   philox_batch(d_c0, n, c1, c2, c3, k0, k1, d_out, (cudaStream_t)cuda_stream);
   if (cudaGetLastError() != cudaSuccess) return NMC_ECUDA;
   if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) return NMC_ECUDA;
+  return NMC_OK;
+}
+
+nmc_status nmc_drift_history(nmc_ctx* x, double* out, long long max, long long* n) {
+  if (!x || !n || (max > 0 && !out)) return NMC_EINVAL;
+  if (!x->configured) return fail(x, NMC_ESTATE, "nmc_drift_history before configuration");
+  NMC_CUDA(x, cudaSetDevice(x->device));
+  const long long have = std::min(x->n_hist, x->hist_cap);
+  *n = x->n_hist;
+  const long long m = std::min(have, max);
+  if (m > 0) {
+    std::vector<unsigned long long> bits(m);
+    NMC_CUDA(x, cudaMemcpyAsync(bits.data(), x->dHist, m * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, x->st()));
+    NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+    for (long long k = 0; k < m; ++k) std::memcpy(&out[k], &bits[k], sizeof(double));
+  }
   return NMC_OK;
 }
 

@@ -154,6 +154,11 @@ void fields_normalize(int8_t* s, long long n, cudaStream_t st);
 void philox_batch(const uint32_t* c0, int n, uint32_t c1, uint32_t c2, uint32_t c3,
                   uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st);
 
+// Per-stabilization drift (bits of non-negative doubles): fold into the per-chain maximum
+// and write the maximum over chains to *hist (if not null).
+void fold_drift(const unsigned long long* stab, unsigned long long* cumulative,
+                unsigned long long* hist, int n_chains, cudaStream_t st);
+
 // Measurement on Gt = e^{dtau K/2} G e^{-dtau K/2}: adds per-chain sums of
 // (energy, ekin, double_occ, s_pipi, density) * sign and sign into acc[chain][8].
 constexpr int kNumObs = 6;   // energy, ekin, docc, s_pipi, density, sign

@@ -23,7 +23,8 @@ EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_field
             "nmc_set_fields_device", "nmc_generate", "nmc_sweep", "nmc_sweep_replay",
             "nmc_measure", "nmc_get_fields", "nmc_get_green", "nmc_get_dims",
             "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_philox", "nmc_philox_device",
-            "nmc_profile", "nmc_kernel_stats", "nmc_green_noalloc", "nmc_last_error",
+            "nmc_drift_history", "nmc_profile", "nmc_kernel_stats", "nmc_green_noalloc",
+            "nmc_last_error",
             "nmc_version", "nmc_destroy")
 
 
@@ -97,6 +98,7 @@ def load():
         "nmc_expk": (i, [i, i, d, d, vp]),
         "nmc_philox": (None, [u32, u32, u32, u32, u32, u32, P(u32)]),
         "nmc_philox_device": (i, [vp, i, u32, u32, u32, u32, u32, vp, vp]),
+        "nmc_drift_history": (i, [vp, vp, ctypes.c_longlong, P(ctypes.c_longlong)]),
         "nmc_profile": (i, [vp, i]),
         "nmc_kernel_stats": (i, [vp, vp, i, P(i), i]),
         "nmc_green_noalloc": (i, [i, i, i, d, vp, vp, i, vp, vp]),
@@ -227,6 +229,14 @@ def nmc_philox_device(d_c0_ptr, n, c1, c2, c3, k0, k1, d_out_ptr, stream=None):
         raise NmcError(st, "nmc_philox_device")
 
 
+def nmc_drift_history(ctx, max_entries=4096):
+    """Per-stabilization drift (max over chains), oldest first."""
+    out = np.zeros(max_entries, dtype=np.float64)
+    n = ctypes.c_longlong(0)
+    _check(ctx, load().nmc_drift_history(ctx, _ptr(out), max_entries, ctypes.byref(n)))
+    return out[:min(n.value, max_entries)].copy()
+
+
 def nmc_profile(ctx, enable):
     _check(ctx, load().nmc_profile(ctx, int(bool(enable))))
 
@@ -325,6 +335,9 @@ class Context:
 
     def restore(self, blob):
         nmc_restore(self.ctx, blob)
+
+    def drift_history(self, max_entries=4096):
+        return nmc_drift_history(self.ctx, max_entries)
 
     def profile(self, enable):
         nmc_profile(self.ctx, enable)
