@@ -40,6 +40,15 @@ DRIFT_BAR = 1e-5
 # (TwoProd by FMA, TwoSum, two cross-term FMAs, two adds), so the pipe's ceiling in
 # algorithmic flop is 80.55 / 12 = 6.71 TFLOP/s.
 PEAK_TFLOPS = {"fp64": 1.259, "fp32": 80.55, "fp32x2": 6.713}
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0  # recipe fallback
+
+
+BF16_PEAK = _bf16_peak()
 PEAK_SOURCE = {
     "fp64": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
     "fp32": "152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (derived)",
@@ -162,15 +171,24 @@ def oracle_rate(cores, steps, warmup):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp32x2": 2, "fp64_ph": 0, "fp32x2_ph": 2}
+# path name -> (precision, particle-hole single spin, gemm_impl)
+PATHS = {"fp64": (0, 0, 0), "fp32": (1, 0, 0), "fp32x2": (2, 0, 0), "fp32x2_simt": (2, 0, 1),
+         "fp64_ph": (0, 1, 0), "fp32x2_ph": (2, 1, 0)}
+# exact-slicing tensor-core products: 7 integer BF16 slices per operand, slice pairs with
+# s + t <= 8 (28 products) issued per algorithmic product
+OZ_PRODUCTS = 28
+
+
+def context(nmc, path, rank, stream):
+    prec, ph, impl = PATHS[path]
+    return nmc.Context(WL.Lx, WL.Ly, WL.t, WL.U, WL.beta, WL.dtau, WL.n_wrap, seed=WL.seed,
+                       n_chains=WL.n_chains, delay_k=WL.delay_k, precision=prec,
+                       drift_tol=1e300, chain_offset=weak_offset(rank, WL.n_chains),
+                       stream=stream.cuda_stream, ph_symmetric=ph, gemm_impl=impl)
 
 
 def run_path(nmc, torch, prec_name, steps, warmup, rank, stream, flush_buf):
-    prec = PRECISIONS[prec_name]
-    c = nmc.Context(WL.Lx, WL.Ly, WL.t, WL.U, WL.beta, WL.dtau, WL.n_wrap, seed=WL.seed,
-                    n_chains=WL.n_chains, delay_k=WL.delay_k, precision=prec,
-                    drift_tol=1e300, chain_offset=weak_offset(rank, WL.n_chains),
-                    stream=stream.cuda_stream, ph_symmetric=prec_name.endswith("_ph"))
+    c = context(nmc, prec_name, rank, stream)
     try:
         c.generate()
         c.sweep(warmup, measure=1)
@@ -199,12 +217,8 @@ def run_e2e(nmc, torch, prec_name, steps, rank, stream):  # noqa: C901
     sweeps, observables and fields back to host, all inside the timed region."""
     import numpy as np
     from paper_2106_00712_gb300.workloads import random_fields
-    prec = PRECISIONS[prec_name]
     fields = random_fields(WL.n_chains, WL.L_tau, WL.N, seed=1000 + rank)
-    c = nmc.Context(WL.Lx, WL.Ly, WL.t, WL.U, WL.beta, WL.dtau, WL.n_wrap, seed=WL.seed,
-                    n_chains=WL.n_chains, delay_k=WL.delay_k, precision=prec,
-                    drift_tol=1e300, chain_offset=weak_offset(rank, WL.n_chains),
-                    stream=stream.cuda_stream, ph_symmetric=prec_name.endswith("_ph"))
+    c = context(nmc, prec_name, rank, stream)
     try:
         c.set_fields(fields)                          # warm the path once
         c.sweep(1, measure=1)
@@ -233,8 +247,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", default="fp64,fp32x2,fp32,fp64_ph,fp32x2_ph")
-    ap.add_argument("--value-paths", default="fp64,fp32x2,fp32",
+    ap.add_argument("--paths", default="fp64,fp32x2,fp32x2_simt,fp32,fp64_ph,fp32x2_ph")
+    ap.add_argument("--value-paths", default="fp64,fp32x2,fp32x2_simt,fp32",
                     help="paths eligible for `value` (the per-spin G of the specification)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -308,26 +322,32 @@ def main():
     st = r["stats"]
     dom = max(st, key=lambda k: st[k][2])          # kernel class with most device time
     launches_total = sum(v[0] for v in st.values())
-    ns = 1 if best.endswith("_ph") else 2
-    base = best[:-3] if best.endswith("_ph") else best
+    prec, ph, impl = PATHS[best]
+    ns = 1 if ph else 2
+    base = {0: "fp64", 1: "fp32", 2: "fp32x2"}[prec]
     per_launch_flop = 2.0 * WL.N ** 3 * ns * WL.n_chains  # batched N x N x N, ns per chain
-    # the dominant GEMM class of the chosen path and the peak of the pipe it runs on
-    gcls = "gemm_df" if base == "fp32x2" else "gemm"
-    g_launch, g_timed, g_ms = st[gcls]
-    achieved = per_launch_flop / (g_ms / max(g_timed, 1) * 1e-3) / 1e12
-    peak = PEAK_TFLOPS[base]
-    traffic = None
-    key = f"{gcls}_{best}"
-    src = "gemm_df.cu" if gcls == "gemm_df" else "gemm.cu"
-    if key in TRAFFIC and TRAFFIC[key]["src"] == src_hash(src):
-        traffic = TRAFFIC[key]["bytes"]
-    kname = {"fp64": "k_gemm<double,64>", "fp32": "k_gemm<float,64>",
-             "fp32x2": "k_gemm_df<64,64> (compensated FP32 pairs)"}[base]
     tot_ms = max(sum(x[2] for x in st.values()), 1e-30)
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_source": PEAK_SOURCE[base], "dominant_class": dom,
-                "share": {k: v[2] / tot_ms for k, v in st.items() if v[0]}}
+    share = {k: v[2] / tot_ms for k, v in st.items() if v[0]}
+    if base == "fp32x2" and impl == 0 and st.get("gemm_tc", (0,))[0]:
+        # tensor-core products: the issued work is OZ_PRODUCTS BF16 slice products each
+        g_launch, g_timed, g_ms = st["gemm_tc"]
+        achieved = OZ_PRODUCTS * per_launch_flop / (g_ms / max(g_timed, 1) * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "kernel": "k_gemm_oz (BF16 mma.sync, exact 7x7-slice products)",
+                    "achieved": achieved, "peak": BF16_PEAK, "unit": "TFLOP/s",
+                    "frac": achieved / BF16_PEAK, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
+                    "algorithmic": f"{OZ_PRODUCTS} BF16 slice products per FP64-class product",
+                    "dominant_class": dom, "share": share}
+    else:
+        gcls = "gemm_df" if base == "fp32x2" else "gemm"
+        g_launch, g_timed, g_ms = st[gcls]
+        achieved = per_launch_flop / (g_ms / max(g_timed, 1) * 1e-3) / 1e12
+        peak = PEAK_TFLOPS[base]
+        kname = {"fp64": "k_gemm<double,64>", "fp32": "k_gemm<float,64>",
+                 "fp32x2": "k_gemm_df<64,64> (compensated FP32 pairs)"}[base]
+        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": PEAK_SOURCE[base], "dominant_class": dom, "share": share}
 
     e2e_dt, h2d, d2h, _ = run_e2e(nmc, torch, best, args.steps, rank, stream)
     e2e = {"value": flips_per_step * args.steps / e2e_dt * world, "unit": UNIT,
@@ -356,6 +376,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32+f64", "fp32x2": "f32x2+f64"}[base],
+            "gemm_impl": {0: "tensor cores (exact BF16 slicing) where N <= 64", 1: "SIMT"}[impl],
             "data": "synthetic",
             "config": {**config, "path": best}, "paths": paths_out,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

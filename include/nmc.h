@@ -70,6 +70,9 @@ typedef struct {
                             lattice G_dn = I - P G_up^T P (P = diag((-1)^{x+y})) exactly,
                             R_dn = 1 + Delta_dn G_up_ii, and G~_dn follows the same way.
                             Same chain, half the work.                           default 0  */
+  int gemm_impl;         /* FP32X2 products with a constant operand: 0 = BF16 tensor cores with
+                            exact integer slicing when N <= 64 (else SIMT), 1 = SIMT
+                            double-float always                                  default 0  */
 } nmc_options;
 
 typedef struct {
@@ -182,7 +185,7 @@ nmc_status nmc_philox_device(const uint32_t* d_c0, int n, uint32_t c1, uint32_t 
 nmc_status nmc_drift_history(nmc_ctx* ctx, double* out, long long max, long long* n);
 
 /* Per-kernel accounting (tracing). Every library kernel launch is counted by class
- * ("gemm", "flip", "qrp", "solve", "measure", "other", "gemm_df"). With profiling enabled, each
+ * ("gemm", "flip", "qrp", "solve", "measure", "other", "gemm_df", "gemm_tc"). With profiling enabled, each
  * launch is also bracketed by CUDA events on the context stream, and nmc_kernel_stats
  * reports the summed device time of the bracketed launches. */
 typedef struct {

@@ -1,0 +1,254 @@
+// FP64-class products on the BF16 tensor cores by exact integer slicing (Ozaki-style
+// error-free splitting; Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 2012).
+//
+// Each row of A (or column of B) is scaled by a power of two 2^e so its entries lie in
+// (-1/2, 1/2), then cut into S integer slices: x = 2^e sum_s a_s 2^{-8s}, |a_s| <= 129.
+// Integers of that size are exact in BF16, a slice product a_s b_t is exact, and a K = 64
+// sum of such products stays below 2^24 and is exact in the FP32 accumulator. The product is
+//     C_ij = 2^{e_i + f_j} sum_g 2^{-8g} P_g(i,j),   P_g = sum_{s+t=g} A_s B_t,
+// with each group g = s + t accumulated separately (at most 7 pairs: every group sum stays
+// below 7.5e6 < 2^24) and the groups combined in double-float in the epilogue. With S = 7
+// and g <= S + 1 (28 slice products) the dropped terms are ~2^-49 of the row/column maxima
+// -- the precision of the double-float SIMT path, at tensor-core throughput.
+//
+// One CTA per N x N matrix (N <= 64, zero-padded to 64), 16 warps, each warp a 16 x 16
+// output block (two m16n8k16 n-tiles) with 7 group accumulators. One operand is a shared
+// constant (e^{-+dtau K}, e^{-+dtau K/2}), sliced once per context; the other is the chain's
+// matrix (FP32 pairs), scaled by the field factors while staged, sliced in shared memory.
+#include <cuda_bf16.h>
+
+#include "nmc_internal.cuh"
+
+namespace nmc {
+
+namespace {
+
+constexpr int kS = 7;          // slices per operand
+constexpr int kG = kS;         // groups g = 2..S+1
+constexpr int kNP = 64;        // padded matrix size
+constexpr int kLd = kNP + 8;   // padded row (bf16) -> conflict-free ldmatrix
+constexpr int kThreads = 512;  // 16 warps
+
+__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
+                                        const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                          uint32_t& r3, const void* p) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+      "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// exponent e with |x| <= 2^e for the largest |x| given (0 -> 0)
+__device__ __forceinline__ int scale_exp(float m) {
+  if (!(m > 0.f)) return 0;
+  int e;
+  frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+  return e;
+}
+
+// Cut v * 2^-e (exact power-of-two scaling of an FP32 pair) into kS integer slices.
+__device__ __forceinline__ void slice_value(df2 v, int e, __nv_bfloat16* out, int stride) {
+  float h = ldexpf(v.hi, 8 - e), l = ldexpf(v.lo, 8 - e);
+  for (int s = 0; s < kS; ++s) {
+    const float a = rintf(h);
+    out[s * stride] = __float2bfloat16_rn(a);  // integer with |a| <= 256: exact
+    // residual (h - a) + l as an exact pair, then scale by 2^8 for the next slice
+    const float d = __fsub_rn(h, a);           // exact (|h - a| <= 1/2)
+    const float t = __fadd_rn(d, l);
+    const float bb = __fsub_rn(t, d);
+    const float err = __fadd_rn(__fsub_rn(d, __fsub_rn(t, bb)), __fsub_rn(l, bb));
+    h = ldexpf(t, 8);
+    l = ldexpf(err, 8);
+  }
+}
+
+__device__ __forceinline__ int field_m_oz(const int8_t* f, long long fstride, int ns, int b,
+                                          int r, int c, int kr, int kc) {
+  const int sg = (ns == 2 && (b & 1)) ? -1 : 1;
+  const int8_t* fb = f + (long long)(ns == 2 ? b >> 1 : b) * fstride;
+  int m = 0;
+  if (kr) m += kr * (fb[r] > 0 ? 1 : -1);
+  if (kc) m += kc * (fb[c] > 0 ? 1 : -1);
+  return sg * m;
+}
+
+// Shared memory: const slices [kS][kNP][kLd] bf16, chain slices [kS][kNP][kLd] bf16,
+// chain staging [kNP][kNP] df2, chain scale exponents [kNP] int.
+constexpr size_t kSliceBytes = (size_t)kS * kNP * kLd * sizeof(__nv_bfloat16);
+constexpr size_t kSmemBytes = 2 * kSliceBytes + (size_t)kNP * kNP * sizeof(df2) + kNP * 4 + 64;
+
+template <bool CONST_A>
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const DfGemmArgs g) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __nv_bfloat16* Cs = (__nv_bfloat16*)smraw;             // constant operand slices
+  __nv_bfloat16* Xs = (__nv_bfloat16*)(smraw + kSliceBytes);  // chain operand slices
+  df2* stage = (df2*)(smraw + 2 * kSliceBytes);
+  int* xexp = (int*)(stage + kNP * kNP);
+  const int N = g.N, b = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+
+  // constant operand slices (prepared with the matching row/column scaling)
+  {
+    const uint4* src = (const uint4*)g.oz_const;
+    uint4* dst = (uint4*)Cs;
+    for (int e = tid; e < (int)(kSliceBytes / 16); e += kThreads) dst[e] = src[e];
+  }
+  // chain operand: stage as FP32 pairs (zero padding), field scaling when it is B
+  const df2* X = CONST_A ? g.B + (long long)b * g.sB : g.A + (long long)b * g.sA;
+  const int ldx = CONST_A ? g.ldb : g.lda;
+  for (int e = tid; e < kNP * kNP; e += kThreads) {
+    const int r = e >> 6, c = e & 63;
+    df2 v = df_zero();
+    if (r < N && c < N) {
+      v = X[(long long)r * ldx + c];
+      if (CONST_A && g.bfields) {
+        const int m = field_m_oz(g.bfields, g.fstride, g.ns, b, r, c, g.br, g.bc);
+        if (m) v = df_mul(v, g.e[m + 2]);
+      }
+    }
+    stage[e] = v;
+  }
+  __syncthreads();
+  // scale exponents: per column of B (chain = B) or per row of A (chain = A)
+  if (tid < kNP) {
+    float mx = 0.f;
+    for (int k = 0; k < kNP; ++k) {
+      const df2 v = CONST_A ? stage[k * kNP + tid] : stage[tid * kNP + k];
+      mx = fmaxf(mx, fabsf(v.hi));
+    }
+    // |hi + lo| <= |hi| (1 + 2^-24): one extra bit of headroom
+    xexp[tid] = scale_exp(mx) + (mx > 0.f ? 1 : 0);
+  }
+  __syncthreads();
+  for (int e = tid; e < kNP * kNP; e += kThreads) {
+    const int r = e >> 6, c = e & 63;
+    const int ex = CONST_A ? xexp[c] : xexp[r];
+    slice_value(stage[e], ex, Xs + r * kLd + c, kNP * kLd);
+  }
+  __syncthreads();
+
+  const __nv_bfloat16* As = CONST_A ? Cs : Xs;
+  const __nv_bfloat16* Bs = CONST_A ? Xs : Cs;
+  const int m0 = (warp >> 2) * 16, n0 = (warp & 3) * 16;
+  float acc[kG][2][4];
+#pragma unroll
+  for (int q = 0; q < kG; ++q)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[q][j][v] = 0.f;
+
+#pragma unroll 1
+  for (int k0 = 0; k0 < kNP; k0 += 16) {
+    uint32_t bf[kS][4];
+#pragma unroll
+    for (int t = 0; t < kS; ++t) {
+      const __nv_bfloat16* pb =
+          Bs + t * kNP * kLd + (k0 + (lane & 7) + ((lane >> 3) & 1) * 8) * kLd + n0 + (lane >> 4) * 8;
+      ldsm_x4_t(bf[t][0], bf[t][1], bf[t][2], bf[t][3], pb);
+    }
+#pragma unroll
+    for (int s = 0; s < kS; ++s) {
+      uint32_t af[4];
+      const __nv_bfloat16* pa = As + s * kNP * kLd + (m0 + (lane & 15)) * kLd + k0 + (lane >> 4) * 8;
+      ldsm_x4(af[0], af[1], af[2], af[3], pa);
+#pragma unroll
+      for (int t = 0; t < kS; ++t)
+        if (s + t < kG) {  // group g = s + t + 2 <= kS + 1
+          mma_bf16(acc[s + t][0], af, bf[t][0], bf[t][1]);
+          mma_bf16(acc[s + t][1], af, bf[t][2], bf[t][3]);
+        }
+    }
+  }
+
+  // epilogue: C = 2^{e_i + f_j} sum_g 2^{-8g} P_g, smallest groups first, in FP32 pairs
+  const int* cexp = g.oz_const_exp;
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = m0 + (lane >> 2) + ((v >> 1) << 3);
+      const int c = n0 + j * 8 + (lane & 3) * 2 + (v & 1);
+      if (i >= N || c >= N) continue;
+      df2 sum = df_zero();
+#pragma unroll
+      for (int q = kG - 1; q >= 0; --q)
+        sum = df_add(sum, df2{ldexpf(acc[q][j][v], -8 * (q + 2)), 0.f});
+      const int ex = CONST_A ? cexp[i] + xexp[c] : xexp[i] + cexp[c];
+      df2 out{ldexpf(sum.hi, ex), ldexpf(sum.lo, ex)};
+      if (g.cfields) {
+        const int m = field_m_oz(g.cfields, g.fstride, g.ns, b, i, c, g.cr, g.cc);
+        if (m) out = df_mul(out, g.e[m + 2]);
+      }
+      const long long idx = (long long)b * g.sC + (long long)i * g.ldc + c;
+      if (g.Cd) {
+        double d = df_to_double(out);
+        if (g.colscale) d *= g.colscale[(long long)b * g.sColscale + c];
+        g.Cd[idx] = d;
+      } else {
+        g.C[idx] = out;
+      }
+    }
+}
+
+// Slices of a constant N x N FP64 matrix for use as A (row scaling, as_b = 0) or as B
+// (column scaling, as_b = 1): out [kS][kNP][kLd] bf16, exponents [kNP].
+__global__ void k_slice_const(const double* M, int N, int as_b, __nv_bfloat16* out, int* exps) {
+  __shared__ int ex[kNP];
+  const int tid = threadIdx.x;
+  if (tid < kNP) {
+    double mx = 0.0;
+    for (int k = 0; k < N && tid < N; ++k)
+      mx = fmax(mx, fabs(as_b ? M[(long long)k * N + tid] : M[(long long)tid * N + k]));
+    ex[tid] = scale_exp((float)mx) + (mx > 0.0 ? 1 : 0);
+    exps[tid] = ex[tid];
+  }
+  __syncthreads();
+  for (int e = tid; e < kS * kNP * kLd; e += blockDim.x) out[e] = __float2bfloat16_rn(0.f);
+  __syncthreads();
+  for (int e = tid; e < kNP * kNP; e += blockDim.x) {
+    const int r = e >> 6, c = e & 63;
+    df2 v = df_zero();
+    if (r < N && c < N) v = df_from_double(M[(long long)r * N + c]);
+    slice_value(v, as_b ? ex[c] : ex[r], out + r * kLd + c, kNP * kLd);
+  }
+}
+
+}  // namespace
+
+size_t oz_const_elems() { return (size_t)kS * kNP * kLd; }
+
+void slice_const(const double* M, int N, int as_b, void* out, int* exps, cudaStream_t st) {
+  k_slice_const<<<1, 256, 0, st>>>(M, N, as_b, (__nv_bfloat16*)out, exps);
+}
+
+bool gemm_oz_supported(int N) { return N <= kNP; }
+
+void gemm_oz(const DfGemmArgs& g, bool const_is_a, cudaStream_t st) {
+  if (g.batch <= 0) return;
+  if (const_is_a) {
+    cudaFuncSetAttribute(k_gemm_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSmemBytes);
+    k_gemm_oz<true><<<g.batch, kThreads, kSmemBytes, st>>>(g);
+  } else {
+    cudaFuncSetAttribute(k_gemm_oz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSmemBytes);
+    k_gemm_oz<false><<<g.batch, kThreads, kSmemBytes, st>>>(g);
+  }
+}
+
+}  // namespace nmc

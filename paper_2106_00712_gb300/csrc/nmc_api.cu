@@ -79,6 +79,10 @@ struct nmc_ctx {
   float *dGf = nullptr, *dT1f = nullptr;
   df2 *dG2 = nullptr, *dT12 = nullptr, *dEm2 = nullptr, *dEp2 = nullptr;
   df2 *dXa = nullptr, *dXb = nullptr, *dEmh2 = nullptr, *dEph2 = nullptr;
+  // tensor-core slices of e^{-dtau K}, e^{+dtau K}, e^{-dtau K/2}, e^{+dtau K/2} as A / as B
+  void* dOz[4][2] = {};
+  int* dOzExp[4][2] = {};
+  bool oz = false;
   std::vector<UDTBuf> slot;  // size nb + 1; entries 1..nb-1 allocated
   UDTBuf spare;
   double* dSign = nullptr;
@@ -94,9 +98,9 @@ struct nmc_ctx {
 
   // per-kernel accounting: launch counts always, CUDA-event brackets when prof is set
   bool prof = false;
-  long long launches[7] = {0, 0, 0, 0, 0, 0, 0};
-  long long timed[7] = {0, 0, 0, 0, 0, 0, 0};
-  double total_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+  long long launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long timed[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double total_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   struct Rec { int cls; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> event_pool;
@@ -131,10 +135,10 @@ nmc_status fail(nmc_ctx* x, nmc_status s, const std::string& msg) {
   } while (0)
 
 enum KernelClass {
-  KC_GEMM = 0, KC_FLIP, KC_QRP, KC_SOLVE, KC_MEASURE, KC_OTHER, KC_GEMM_DF, KC_COUNT
+  KC_GEMM = 0, KC_FLIP, KC_QRP, KC_SOLVE, KC_MEASURE, KC_OTHER, KC_GEMM_DF, KC_GEMM_TC, KC_COUNT
 };
 const char* const kKernelClassNames[KC_COUNT] = {"gemm", "flip", "qrp", "solve", "measure",
-                                                 "other", "gemm_df"};
+                                                 "other", "gemm_df", "gemm_tc"};
 
 cudaEvent_t pool_event(nmc_ctx* x) {
   if (!x->event_pool.empty()) {
@@ -184,6 +188,9 @@ void free_all(nmc_ctx* x) {
   x->dG = x->dT1 = x->dX = x->dX2 = x->dTp = x->dM1 = x->dXs = x->dY = x->dWS = nullptr;
   x->dGf = x->dT1f = nullptr;
   x->dG2 = x->dT12 = x->dEm2 = x->dEp2 = x->dXa = x->dXb = x->dEmh2 = x->dEph2 = nullptr;
+  for (int a = 0; a < 4; ++a)
+    for (int r = 0; r < 2; ++r) x->dOz[a][r] = nullptr, x->dOzExp[a][r] = nullptr;
+  x->oz = false;
   x->slot.clear();
   x->spare = UDTBuf{};
   x->dSign = nullptr;
@@ -250,6 +257,15 @@ nmc_status alloc_all(nmc_ctx* x) {
     NMC_TRY(dalloc(x, &x->dXb, mats));
     NMC_TRY(dalloc(x, &x->dEmh2, NN));
     NMC_TRY(dalloc(x, &x->dEph2, NN));
+    x->oz = x->opt.gemm_impl == 0 && gemm_oz_supported(x->N);
+    if (x->oz)
+      for (int a = 0; a < 4; ++a)
+        for (int r = 0; r < 2; ++r) {
+          uint16_t* p = nullptr;
+          NMC_TRY(dalloc(x, &p, oz_const_elems()));
+          x->dOz[a][r] = p;
+          NMC_TRY(dalloc(x, &x->dOzExp[a][r], 64));
+        }
   }
   x->slot.assign(x->nb + 1, UDTBuf{});
   auto alloc_udt = [&](UDTBuf& u) -> nmc_status {
@@ -284,6 +300,11 @@ nmc_status alloc_all(nmc_ctx* x) {
     split_to_df(x->dEp, x->dEp2, NN, st);
     split_to_df(x->dEmh, x->dEmh2, NN, st);
     split_to_df(x->dEph, x->dEph2, NN, st);
+    if (x->oz) {
+      const double* src[4] = {x->dEm, x->dEp, x->dEmh, x->dEph};
+      for (int a = 0; a < 4; ++a)
+        for (int r = 0; r < 2; ++r) slice_const(src[a], x->N, r, x->dOz[a][r], x->dOzExp[a][r], st);
+    }
   }
   NMC_CUDA(x, cudaGetLastError());
   NMC_CUDA(x, cudaStreamSynchronize(st));
@@ -360,6 +381,21 @@ DfGemmArgs df_base(const nmc_ctx* x, const df2* A, long long sA, const df2* B, l
   return g;
 }
 
+enum ConstId { OZ_EM = 0, OZ_EP = 1, OZ_EMH = 2, OZ_EPH = 3 };
+
+// Double-float product with one constant operand: tensor cores (exact BF16 slicing) when
+// available for this N, else the SIMT double-float kernel.
+void df_gemm(nmc_ctx* x, DfGemmArgs& g, int const_id, bool const_is_a) {
+  cudaStream_t st = x->st();
+  if (x->oz) {
+    g.oz_const = x->dOz[const_id][const_is_a ? 0 : 1];
+    g.oz_const_exp = x->dOzExp[const_id][const_is_a ? 0 : 1];
+    launch(x, KC_GEMM_TC, [&] { gemm_oz(g, const_is_a, st); });
+  } else {
+    launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
+  }
+}
+
 UDTView identity_view(const nmc_ctx* x) { return UDTView{x->dI, 0, x->dOnes, 0, x->dI, 0}; }
 UDTView view_of(const nmc_ctx* x, const UDTBuf& b) {
   return UDTView{b.U, x->NN(), b.D, x->N, b.T, x->NN()};
@@ -375,18 +411,18 @@ void wrap(nmc_ctx* x, int l, bool up) {
       DfGemmArgs g = df_base(x, x->dEm2, 0, x->dG2, NN);
       g.C = x->dT12;
       g.bfields = fl; g.br = 1; g.bc = -1;
-      launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
+      df_gemm(x, g, OZ_EM, true);
       DfGemmArgs h = df_base(x, x->dT12, NN, x->dEp2, 0);
       h.C = x->dG2;
-      launch(x, KC_GEMM_DF, [&] { gemm_df(h, st); });
+      df_gemm(x, h, OZ_EP, false);
     } else {   // T1 = Ep G; G = e^-V (T1 Em) e^V
       DfGemmArgs g = df_base(x, x->dEp2, 0, x->dG2, NN);
       g.C = x->dT12;
-      launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
+      df_gemm(x, g, OZ_EP, true);
       DfGemmArgs h = df_base(x, x->dT12, NN, x->dEm2, 0);
       h.C = x->dG2;
       h.cfields = fl; h.cr = -1; h.cc = 1;
-      launch(x, KC_GEMM_DF, [&] { gemm_df(h, st); });
+      df_gemm(x, h, OZ_EM, false);
     }
     return;
   }
@@ -478,7 +514,7 @@ void stack_update(nmc_ctx* x, int j, const UDTView& src, const UDTBuf& dst, bool
       } else {
         g.C = bufs[k & 1];
       }
-      launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
+      df_gemm(x, g, OZ_EM, true);
       cur = bufs[k & 1];
       scur = NN;
     }
@@ -560,10 +596,10 @@ void measure_now(nmc_ctx* x) {
   if (x->dfp()) {  // G~ = e^{dtau K/2} G e^{-dtau K/2} from the pair copy of the recomputed G
     DfGemmArgs g = df_base(x, x->dEph2, 0, x->dG2, NN);
     g.C = x->dT12;
-    launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
+    df_gemm(x, g, OZ_EPH, true);
     DfGemmArgs h = df_base(x, x->dT12, NN, x->dEmh2, 0);
     h.Cd = x->dM1;
-    launch(x, KC_GEMM_DF, [&] { gemm_df(h, st); });
+    df_gemm(x, h, OZ_EMH, false);
     launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), x->ns(), st); });
     return;
   }
@@ -750,6 +786,7 @@ void nmc_default_options(nmc_options* o) {
   o->chain_offset = 0;
   o->cuda_stream = nullptr;
   o->ph_symmetric = 0;
+  o->gemm_impl = 0;
 }
 
 nmc_status nmc_create(int Lx, int Ly, double t, double U, double beta, double dtau, int n_wrap,
@@ -789,7 +826,8 @@ nmc_status nmc_configure(nmc_ctx* x, const nmc_options* o) {
   nmc_default_options(&n);
   if (o) n = *o;
   if (n.n_chains < 1 || n.delay_k < 1 || (n.precision != NMC_FP64 && n.precision != NMC_FP32 && n.precision != NMC_FP32X2) ||
-      n.chain_offset < 0 || n.n_chains > (1 << 20) || (n.ph_symmetric != 0 && n.ph_symmetric != 1))
+      n.chain_offset < 0 || n.n_chains > (1 << 20) || (n.ph_symmetric != 0 && n.ph_symmetric != 1) ||
+      (n.gemm_impl != 0 && n.gemm_impl != 1))
     return fail(x, NMC_EINVAL, "invalid nmc_options");
   x->opt = n;
   clamp_delay(x);

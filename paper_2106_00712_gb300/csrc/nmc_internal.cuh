@@ -108,8 +108,18 @@ struct DfGemmArgs {
   long long fstride = 0;
   int ns = 2;  // spins per chain in the batch
   df2 e[5];    // e^{m lam}, m = -2..2
+  // tensor-core path: integer BF16 slices of the constant operand and their scale
+  // exponents (row exponents when it is A, column exponents when it is B)
+  const void* oz_const = nullptr;
+  const int* oz_const_exp = nullptr;
 };
 void gemm_df(const DfGemmArgs& g, cudaStream_t st);
+// Same product on the BF16 tensor cores by exact integer slicing (N <= 64); the constant
+// operand (A if const_is_a, else B) is given by oz_const / oz_const_exp.
+void gemm_oz(const DfGemmArgs& g, bool const_is_a, cudaStream_t st);
+bool gemm_oz_supported(int N);
+size_t oz_const_elems();  // bf16 elements of one sliced constant
+void slice_const(const double* M, int N, int as_b, void* out, int* exps, cudaStream_t st);
 void split_to_df(const double* x, df2* y, long long n, cudaStream_t st);
 
 // ---------------------------------------------------------------------------- UDT

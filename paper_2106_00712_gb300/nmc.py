@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
     _fields_ = [("n_chains", ctypes.c_int), ("delay_k", ctypes.c_int),
                 ("precision", ctypes.c_int), ("drift_tol", ctypes.c_double),
                 ("chain_offset", ctypes.c_longlong), ("cuda_stream", ctypes.c_void_p),
-                ("ph_symmetric", ctypes.c_int)]
+                ("ph_symmetric", ctypes.c_int), ("gemm_impl", ctypes.c_int)]
 
 
 class Est(ctypes.Structure):
@@ -277,13 +277,14 @@ class Context:
 
     def __init__(self, Lx, Ly, t, U, beta, dtau, n_wrap, seed=0, n_chains=1, delay_k=16,
                  precision=NMC_FP64, drift_tol=0.0, chain_offset=0, stream=None,
-                 ph_symmetric=0):
+                 ph_symmetric=0, gemm_impl=0):
         self.ctx = nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed)
         o = nmc_default_options()
         o.n_chains, o.delay_k, o.precision = n_chains, delay_k, precision
         o.drift_tol, o.chain_offset = drift_tol, chain_offset
         o.cuda_stream = stream
         o.ph_symmetric = int(ph_symmetric)
+        o.gemm_impl = int(gemm_impl)
         try:
             nmc_configure(self.ctx, o)
         except Exception:

@@ -278,6 +278,26 @@ def test_fp32x2_8x8_256_chains_sampled(nmc):
                  check_chains=[3, 200], precision=nmc.NMC_FP32X2, g_rel=G_REL_X2)
 
 
+def test_fp32x2_tensor_core_slicing_equals_simt(nmc):
+    """The exact-slicing BF16 tensor-core products and the SIMT double-float products give
+    the same chain and the same G to FP64-class accuracy (8x8, beta=4, 3 sweeps)."""
+    model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=3)
+    gs = {}
+    for impl in (0, 1):
+        with _ctx(nmc, model, n_chains=8, precision=nmc.NMC_FP32X2, gemm_impl=impl) as c:
+            c.generate()
+            c.sweep(3, measure=1)
+            st = c.kernel_stats()
+            assert st["gemm_tc" if impl == 0 else "gemm_df"][0] > 0
+            assert st["gemm_df" if impl == 0 else "gemm_tc"][0] == 0
+            gs[impl] = (c.fields(), [c.green(ch, sp) for ch in range(8) for sp in (0, 1)],
+                        c.measure().max_drift)
+    np.testing.assert_array_equal(gs[0][0], gs[1][0])
+    for a, b in zip(gs[0][1], gs[1][1]):
+        assert np.max(np.abs(a - b)) < 1e-9
+    assert gs[0][2] <= 1e-5
+
+
 # particle-hole single-spin mode: spin down derived from spin up, same chain
 
 @pytest.mark.parametrize("prec", [0, 2])
