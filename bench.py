@@ -251,6 +251,8 @@ def main():
     ap.add_argument("--value-paths", default="fp64,fp32x2,fp32x2_simt,fp32",
                     help="paths eligible for `value` (the per-spin G of the specification)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests in the serving leg (0 = skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -355,6 +357,12 @@ def main():
            "path": best, "includes": "set_fields(host) + stack build + K sweeps + "
                                      "measure(host) + get_fields(host)"}
 
+    serve = None
+    if args.serve_requests > 0 and world == 1:
+        from paper_2106_00712_gb300.serving import serve_stream
+        serve = serve_stream(args.serve_requests)
+        serve["workload"] = ("Poisson stream, L in {6,8,10,12}, beta in {2,4,6}, U in {2,4,8}, "
+                             "dtau 0.1, 16 chains, 20 + 50 sweeps, FP32X2, 100 GB budget")
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -380,6 +388,7 @@ def main():
             "data": "synthetic",
             "config": {**config, "path": best}, "paths": paths_out,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "serve": serve,
             "gpu_launches": launches_total}
     print(json.dumps(line), flush=True)
     if world > 1:

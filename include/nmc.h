@@ -136,6 +136,24 @@ nmc_status nmc_generate(nmc_ctx* ctx, int mode, const void* model);
  * Returns NMC_ENUMERIC if the drift is non-finite or above drift_tol (state is kept). */
 nmc_status nmc_sweep(nmc_ctx* ctx, int n_sweeps, int measure);
 
+/* As nmc_sweep, but only enqueues the work on the context stream and returns; the drift
+ * check happens at nmc_sync. Host state (sweep counter, direction) advances immediately,
+ * so further calls queue behind. Used by the serving loop to keep many contexts' work in
+ * flight on different streams at once. */
+nmc_status nmc_sweep_async(nmc_ctx* ctx, int n_sweeps, int measure);
+
+/* *idle = 1 if all work enqueued on the context stream has finished, else 0. */
+nmc_status nmc_query(nmc_ctx* ctx, int* idle);
+
+/* Wait for the context stream, then check the drift as nmc_sweep does. */
+nmc_status nmc_sync(nmc_ctx* ctx);
+
+/* Host only: device bytes nmc_configure allocates for this problem and these options
+ * (opts NULL = defaults), excluding the growable measurement series (8 doubles per chain
+ * per measured sweep). For admission control. */
+nmc_status nmc_footprint(int Lx, int Ly, double t, double U, double beta, double dtau,
+                         int n_wrap, const nmc_options* opts, size_t* bytes);
+
 /* One sweep that applies the given accept decisions instead of its own
  * (uint8 [n_chains][L_tau][N], nonzero = flip; n = element count). The library still
  * evaluates its own ratio for every attempt and counts disagreements

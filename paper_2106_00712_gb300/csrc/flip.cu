@@ -47,7 +47,7 @@ __device__ void flush(T* G, const T* Ap, const T* Bp, int m, int N, int KK, long
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ int s_accept;
+  __shared__ int s_accept[2];  // by attempt parity: see the loop
   __shared__ double s_coef[2];
   __shared__ double s_sign;
   __shared__ unsigned long long s_cnt[3];
@@ -88,6 +88,10 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
   }
   __syncthreads();
 
+  // The accept flag is double-buffered by attempt parity: after a rejection there is one
+  // barrier per attempt, so thread 0 may write the next attempt's flag while slower threads
+  // still read this one. It cannot write this slot again (attempt i+2) before every thread
+  // has passed attempt i+1's barrier, which follows its read of attempt i's flag.
   int m = 0;
   for (int i = 0; i < N; ++i) {
     if (threadIdx.x < 32) {
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
           if (acc != mine) s_cnt[2]++;
         }
         s_cnt[0]++;
-        s_accept = acc ? 1 : 0;
+        s_accept[i & 1] = acc ? 1 : 0;
         if (acc) {
           s_coef[0] = -du / Ru;
           s_coef[1] = -dd / Rd;
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
       }
     }
     __syncthreads();
-    if (s_accept) {
+    if (s_accept[i & 1]) {
       const T coef[2] = {(T)s_coef[0], (T)s_coef[1]};
       for (int t = threadIdx.x; t < 2 * ns * N; t += blockDim.x) {
         const int sp = t / (2 * N);
@@ -205,7 +209,7 @@ __device__ void flush_df(df2* G, const df2* Ap, const df2* Bp, int m, int N, int
 
 __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ int s_accept;
+  __shared__ int s_accept[2];  // by attempt parity: see the loop
   __shared__ df2 s_coef[2];
   __shared__ double s_sign;
   __shared__ unsigned long long s_cnt[3];
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
         if (acc_flip != mine) s_cnt[2]++;
       }
       s_cnt[0]++;
-      s_accept = acc_flip ? 1 : 0;
+      s_accept[i & 1] = acc_flip ? 1 : 0;
       if (acc_flip) {
         s_coef[0] = df_neg(df_mul(du, df_rcp(Ru)));
         s_coef[1] = df_neg(df_mul(dd, df_rcp(Rd)));
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
       }
     }
     __syncthreads();
-    if (s_accept) {
+    if (s_accept[i & 1]) {
       for (int t = threadIdx.x; t < ns * N; t += blockDim.x) {
         const int sp = t / N, r = t % N;
         const df2* Gsp = G + sp * NN;
@@ -353,7 +357,7 @@ size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem, int ns) {
 template <typename T>
 void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st) {
   const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(T), f.g_in_smem, f.ns);
-  cudaFuncSetAttribute(k_flip<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  allow_max_dynamic_smem((const void*)k_flip<T>);
   k_flip<T><<<n_chains, kThreads, bytes, st>>>(f);
 }
 
@@ -363,7 +367,7 @@ template void flip_slice<float>(const FlipArgs<float>&, int, cudaStream_t);
 template <>
 void flip_slice<df2>(const FlipArgs<df2>& f, int n_chains, cudaStream_t st) {
   const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(df2), f.g_in_smem, f.ns);
-  cudaFuncSetAttribute(k_flip_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  allow_max_dynamic_smem((const void*)k_flip_df);
   k_flip_df<<<n_chains, kThreads, bytes, st>>>(f);
 }
 

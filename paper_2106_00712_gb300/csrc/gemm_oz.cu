@@ -241,12 +241,10 @@ bool gemm_oz_supported(int N) { return N <= kNP; }
 void gemm_oz(const DfGemmArgs& g, bool const_is_a, cudaStream_t st) {
   if (g.batch <= 0) return;
   if (const_is_a) {
-    cudaFuncSetAttribute(k_gemm_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kSmemBytes);
+    allow_max_dynamic_smem((const void*)k_gemm_oz<true>);
     k_gemm_oz<true><<<g.batch, kThreads, kSmemBytes, st>>>(g);
   } else {
-    cudaFuncSetAttribute(k_gemm_oz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kSmemBytes);
+    allow_max_dynamic_smem((const void*)k_gemm_oz<false>);
     k_gemm_oz<false><<<g.batch, kThreads, kSmemBytes, st>>>(g);
   }
 }

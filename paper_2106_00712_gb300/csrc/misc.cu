@@ -1,5 +1,9 @@
 // Small device kernels: Philox field initialisation, conversions, and the equal-time
-// estimators.
+// estimators; the dynamic shared-memory limit helper.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "nmc_internal.cuh"
 
 namespace nmc {
@@ -162,6 +166,33 @@ int grid_for(long long n) {
 }
 
 }  // namespace
+
+// The dynamic shared-memory limit is a per-function, per-device attribute and is not
+// stream-ordered: lowering it for one launch can break a larger launch of the same kernel
+// still queued on another stream. So each kernel's limit is raised once per device to the
+// device's opt-in maximum and never lowered.
+void allow_max_dynamic_smem(const void* func) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({func, dev})) return;
+  int optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, func) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  // the dynamic limit excludes the kernel's static shared memory
+  const int limit = optin - (int)fa.sharedSizeBytes;
+  if (limit > 0 &&
+      cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) == cudaSuccess)
+    done.insert({func, dev});
+  else
+    cudaGetLastError();
+}
 
 void init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0, uint32_t k1,
                  long long chain_offset, cudaStream_t st) {

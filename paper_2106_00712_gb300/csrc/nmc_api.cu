@@ -63,6 +63,8 @@ struct nmc_ctx {
   int kk = 16, g_in_smem = 0;
   int device = -1;
   bool configured = false, have_fields = false;
+  bool dry = false;          // size-only allocation pass (nmc_footprint)
+  size_t dry_bytes = 0;
   long long sweep_counter = 0;  // Philox counter word 1
   long long phase = 0;          // sweeps since the fields were set (parity = direction)
   std::string err;
@@ -179,8 +181,11 @@ void resolve_events(nmc_ctx* x) {
   x->recs.clear();
 }
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the context stream):
+// creating or destroying one context does not synchronise the device, so other contexts'
+// work on other streams keeps running (the serving loop depends on this).
 void free_all(nmc_ctx* x) {
-  for (void* p : x->allocs) cudaFree(p);
+  for (void* p : x->allocs) cudaFreeAsync(p, x->st());
   x->allocs.clear();
   x->dK = x->dEm = x->dEp = x->dEmh = x->dEph = x->dI = x->dOnes = nullptr;
   x->dEmf = x->dEpf = nullptr;
@@ -208,11 +213,16 @@ void free_all(nmc_ctx* x) {
 
 template <typename T>
 nmc_status dalloc(nmc_ctx* x, T** p, size_t count) {
+  if (x->dry) {
+    x->dry_bytes += ((std::max<size_t>(count, 1) * sizeof(T) + 511) / 512) * 512;
+    *p = nullptr;
+    return NMC_OK;
+  }
   void* q = nullptr;
-  const cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  const cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), x->st());
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(x, NMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return fail(x, NMC_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
   }
   x->allocs.push_back(q);
   *p = (T*)q;
@@ -220,8 +230,10 @@ nmc_status dalloc(nmc_ctx* x, T** p, size_t count) {
 }
 
 nmc_status alloc_all(nmc_ctx* x) {
-  free_all(x);
-  NMC_CUDA(x, cudaGetDevice(&x->device));
+  if (!x->dry) {
+    free_all(x);
+    NMC_CUDA(x, cudaGetDevice(&x->device));
+  }
   const long long NN = x->NN();
   const int B = x->batch();
   const size_t mats = (size_t)B * NN;
@@ -282,6 +294,7 @@ nmc_status alloc_all(nmc_ctx* x) {
   NMC_TRY(dalloc(x, &x->dDriftStab, x->chains()));
   x->hist_cap = 4096;
   NMC_TRY(dalloc(x, &x->dHist, x->hist_cap));
+  if (x->dry) return NMC_OK;
 
   cudaStream_t st = x->st();
   const size_t mb = NN * sizeof(double);
@@ -687,23 +700,22 @@ nmc_status after_fields(nmc_ctx* x) {
 nmc_status ensure_series(nmc_ctx* x, long long need) {
   if (need <= x->series_cap) return NMC_OK;
   long long cap = std::max<long long>(need, 2 * x->series_cap);
-  cap = std::max<long long>(cap, 16);
+  cap = std::max<long long>(cap, 64);
   double* p = nullptr;
   const size_t bytes = (size_t)cap * x->chains() * 8 * sizeof(double);
-  const cudaError_t e = cudaMalloc(&p, bytes);
+  const cudaError_t e = cudaMallocAsync((void**)&p, bytes, x->st());
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(x, NMC_ENOMEM, "series buffer: cudaMalloc failed");
+    return fail(x, NMC_ENOMEM, "series buffer: cudaMallocAsync failed");
   }
   NMC_CUDA(x, cudaMemsetAsync(p, 0, bytes, x->st()));
   if (x->dSeries && x->n_series > 0)
     NMC_CUDA(x, cudaMemcpyAsync(p, x->dSeries, (size_t)x->n_series * x->chains() * 8 * sizeof(double),
                                 cudaMemcpyDeviceToDevice, x->st()));
-  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
-  if (x->dSeries) {
+  if (x->dSeries) {  // stream-ordered: freed after the copy above
     x->allocs.erase(std::remove(x->allocs.begin(), x->allocs.end(), (void*)x->dSeries),
                     x->allocs.end());
-    cudaFree(x->dSeries);
+    cudaFreeAsync(x->dSeries, x->st());
   }
   x->dSeries = p;
   x->allocs.push_back(p);
@@ -730,7 +742,7 @@ nmc_status check_drift(nmc_ctx* x) {
   return NMC_OK;
 }
 
-nmc_status run_sweeps(nmc_ctx* x, int n, int meas, const uint8_t* replay) {
+nmc_status run_sweeps(nmc_ctx* x, int n, int meas, const uint8_t* replay, bool wait = true) {
   if (meas) NMC_TRY(ensure_series(x, x->n_series + n));
   for (int s = 0; s < n; ++s) {
     if (x->phase % 2 == 0) sweep_up(x, meas != 0, replay);
@@ -740,6 +752,7 @@ nmc_status run_sweeps(nmc_ctx* x, int n, int meas, const uint8_t* replay) {
     ++x->sweep_counter;
     if (meas) ++x->n_series;
   }
+  if (!wait) return NMC_OK;
   NMC_CUDA(x, cudaStreamSynchronize(x->st()));
   return check_drift(x);
 }
@@ -872,6 +885,49 @@ nmc_status nmc_sweep(nmc_ctx* x, int n_sweeps, int measure) {
   if (!x->have_fields) return fail(x, NMC_ESTATE, "nmc_sweep before fields were set");
   NMC_TRY(ensure_configured(x));
   return run_sweeps(x, n_sweeps, measure, nullptr);
+}
+
+nmc_status nmc_sweep_async(nmc_ctx* x, int n_sweeps, int measure) {
+  if (!x || n_sweeps < 0) return NMC_EINVAL;
+  if (!x->have_fields) return fail(x, NMC_ESTATE, "nmc_sweep_async before fields were set");
+  NMC_TRY(ensure_configured(x));
+  return run_sweeps(x, n_sweeps, measure, nullptr, false);
+}
+
+nmc_status nmc_query(nmc_ctx* x, int* idle) {
+  if (!x || !idle) return NMC_EINVAL;
+  if (!x->configured) return fail(x, NMC_ESTATE, "nmc_query before configuration");
+  NMC_CUDA(x, cudaSetDevice(x->device));
+  const cudaError_t e = cudaStreamQuery(x->st());
+  if (e == cudaSuccess) { *idle = 1; return NMC_OK; }
+  if (e == cudaErrorNotReady) { cudaGetLastError(); *idle = 0; return NMC_OK; }
+  return fail(x, NMC_ECUDA, std::string("cudaStreamQuery: ") + cudaGetErrorString(e));
+}
+
+nmc_status nmc_sync(nmc_ctx* x) {
+  if (!x) return NMC_EINVAL;
+  if (!x->configured) return fail(x, NMC_ESTATE, "nmc_sync before configuration");
+  NMC_CUDA(x, cudaSetDevice(x->device));
+  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  return check_drift(x);
+}
+
+nmc_status nmc_footprint(int Lx, int Ly, double t, double U, double beta, double dtau,
+                         int n_wrap, const nmc_options* opts, size_t* bytes) {
+  if (!bytes) return NMC_EINVAL;
+  nmc_ctx* x = nullptr;
+  const nmc_status st = nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, 0, &x);
+  if (st != NMC_OK) return st;
+  nmc_options o;
+  nmc_default_options(&o);
+  if (opts) o = *opts;
+  x->opt = o;
+  clamp_delay(x);
+  x->dry = true;
+  alloc_all(x);
+  *bytes = x->dry_bytes;
+  delete x;
+  return NMC_OK;
 }
 
 nmc_status nmc_sweep_replay(nmc_ctx* x, const uint8_t* accept, size_t n, int measure) {

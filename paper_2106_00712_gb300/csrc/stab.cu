@@ -289,7 +289,7 @@ void qrp_udt(const double* X, double* U, double* D, double* Tp, double* ws, int 
   const size_t big = small + 2 * (size_t)N * N * sizeof(double);
   const int use_smem = big <= kSmemLimit;
   const size_t bytes = use_smem ? big : small;
-  cudaFuncSetAttribute(k_qrp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  allow_max_dynamic_smem((const void*)k_qrp);
   k_qrp<<<batch, kThreads, bytes, st>>>(X, U, D, Tp, ws, N, use_smem);
 }
 
@@ -298,8 +298,7 @@ void solve_stab(const double* X, const double* UR, long long sUR, const double* 
   const size_t big = 2 * (size_t)N * N * sizeof(double);
   const int use_smem = big <= kSmemLimit;
   const size_t bytes = use_smem ? big : 0;
-  if (use_smem)
-    cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  allow_max_dynamic_smem((const void*)k_solve);
   k_solve<<<batch, kThreads, bytes, st>>>(X, UR, sUR, DR, sDR, Y, ws, N, use_smem);
 }
 

@@ -20,7 +20,8 @@ NMC_FP64, NMC_FP32, NMC_FP32X2 = 0, 1, 2
 
 # every symbol include/nmc.h declares
 EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_fields",
-            "nmc_set_fields_device", "nmc_generate", "nmc_sweep", "nmc_sweep_replay",
+            "nmc_set_fields_device", "nmc_generate", "nmc_sweep", "nmc_sweep_async",
+            "nmc_query", "nmc_sync", "nmc_footprint", "nmc_sweep_replay",
             "nmc_measure", "nmc_get_fields", "nmc_get_green", "nmc_get_dims",
             "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_philox", "nmc_philox_device",
             "nmc_drift_history", "nmc_profile", "nmc_kernel_stats", "nmc_green_noalloc",
@@ -88,6 +89,10 @@ def load():
         "nmc_set_fields_device": (i, [vp, vp, sz]),
         "nmc_generate": (i, [vp, i, vp]),
         "nmc_sweep": (i, [vp, i, i]),
+        "nmc_sweep_async": (i, [vp, i, i]),
+        "nmc_query": (i, [vp, P(i)]),
+        "nmc_sync": (i, [vp]),
+        "nmc_footprint": (i, [i, i, d, d, d, d, i, P(Options), P(sz)]),
         "nmc_sweep_replay": (i, [vp, vp, sz, i]),
         "nmc_measure": (i, [vp, vp, P(Obs)]),
         "nmc_get_fields": (i, [vp, vp, sz]),
@@ -159,6 +164,29 @@ def nmc_generate(ctx, mode=0, model=None):
 
 def nmc_sweep(ctx, n_sweeps, measure=1):
     _check(ctx, load().nmc_sweep(ctx, n_sweeps, measure))
+
+
+def nmc_sweep_async(ctx, n_sweeps, measure=1):
+    _check(ctx, load().nmc_sweep_async(ctx, n_sweeps, measure))
+
+
+def nmc_query(ctx):
+    idle = ctypes.c_int(0)
+    _check(ctx, load().nmc_query(ctx, ctypes.byref(idle)))
+    return bool(idle.value)
+
+
+def nmc_sync(ctx):
+    _check(ctx, load().nmc_sync(ctx))
+
+
+def nmc_footprint(Lx, Ly, t, U, beta, dtau, n_wrap, opts=None):
+    n = ctypes.c_size_t(0)
+    st = load().nmc_footprint(Lx, Ly, t, U, beta, dtau, n_wrap,
+                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(n))
+    if st != NMC_OK:
+        raise NmcError(st, "nmc_footprint")
+    return n.value
 
 
 def nmc_sweep_replay(ctx, accept, measure=1):
@@ -318,6 +346,15 @@ class Context:
 
     def sweep(self, n, measure=1):
         nmc_sweep(self.ctx, n, measure)
+
+    def sweep_async(self, n, measure=1):
+        nmc_sweep_async(self.ctx, n, measure)
+
+    def idle(self):
+        return nmc_query(self.ctx)
+
+    def sync(self):
+        nmc_sync(self.ctx)
 
     def sweep_replay(self, accept, measure=1):
         nmc_sweep_replay(self.ctx, accept, measure)
