@@ -3,7 +3,7 @@
  * network-initialized Monte Carlo (arXiv 2106.00712), run on one NVIDIA GB300 (sm_103a).
  *
  * The operation is the Markov chain over the discrete Hubbard-Stratonovich field s(i,l)
- * of the half-filled Hubbard model (Eq. 3) on a periodic Lx x Ly square lattice, with
+ * of the half-filled Hubbard model (Eq. 3) on a periodic square or honeycomb lattice, with
  * weight prod_sigma Det[I + B^sigma_L ... B^sigma_1] (Supplemental Material Sec. I.2,
  * partition function in determinant form) and B^sigma_l = e^{-dtau K} e^{sigma lam
  * diag s(.,l)}, cosh lam = e^{dtau U/2} (Sec. I.2, discrete HS transform). One sweep gives
@@ -58,6 +58,17 @@ typedef enum {
                         FP32 pipes; QR, recompute, ratios and measurement in FP64         */
 } nmc_precision;
 
+/* Lattices of Eq. 3 (both periodic and bipartite; K_ij = -t per nearest-neighbour pair,
+ * set once, so a length-2 direction has one bond and a length-1 direction none).
+ *   NMC_SQUARE:    Lx x Ly sites, i = x + Lx*y; sublattice parity (x + y) mod 2.
+ *   NMC_HONEYCOMB: Lx x Ly cells of two sites (the honeycomb lattice of the paper's
+ *                  Hubbard runs, "Models" and SM Sec. II.1: L x L cells, 2 L^2 sites),
+ *                  i = 2 (x + Lx*y) + sub; the A site (sub 0) of cell (x,y) bonds to the
+ *                  B sites (sub 1) of cells (x,y), (x-1,y), (x,y-1); parity = sub.
+ * The estimators' staggered sign p_i = (-1)^parity: S(pi,pi) on the square lattice and
+ * the antiferromagnetic S(Gamma) (Eq. 4 with opposite signs on A and B) on the honeycomb. */
+typedef enum { NMC_SQUARE = 0, NMC_HONEYCOMB = 1 } nmc_lattice;
+
 typedef struct {
   int n_chains;          /* independent chains held by this context (>= 1)       default 1  */
   int delay_k;           /* accepted flips folded per rank-k delayed update (>= 1) def. 16   */
@@ -67,7 +78,7 @@ typedef struct {
   long long chain_offset;/* global index of local chain 0 (Philox counter word 2) def. 0   */
   void* cuda_stream;     /* cudaStream_t for all device work                     def. NULL */
   int ph_symmetric;      /* 1: propagate spin up only; at half filling on the bipartite
-                            lattice G_dn = I - P G_up^T P (P = diag((-1)^{x+y})) exactly,
+                            lattice G_dn = I - P G_up^T P (P = diag of sublattice signs) exactly,
                             R_dn = 1 + Delta_dn G_up_ii, and G~_dn follows the same way.
                             Same chain, half the work.                           default 0  */
   int gemm_impl;         /* FP32X2 products with a constant operand: 0 = BF16 tensor cores with
@@ -94,16 +105,18 @@ typedef struct {
   long long n_disagree;  /* replay sweeps: attempts whose own decision differed            */
 } nmc_obs;
 
-/* Create a context for the periodic Lx x Ly square lattice with hopping t and
+/* Create a context for the periodic lattice (nmc_lattice, Lx x Ly) with hopping t and
  * interaction U (Eq. 3) at inverse temperature beta, Trotter step dtau (Sec. I.2:
  * L_tau = beta/dtau slices), stabilization every n_wrap slices, Philox seed `seed`.
  * Host-side set-up (K, e^{-+dtau K}, e^{-+dtau K/2} by a Jacobi eigensolver, lam) happens
  * here; device memory is allocated by nmc_configure / the first call that needs it.
- * NMC_EINVAL: Lx*Ly < 2, Lx or Ly odd and > 1 (lattice must be bipartite), t <= 0,
+ * lattice: nmc_lattice; N = Lx*Ly (square) or 2*Lx*Ly (honeycomb).
+ * NMC_EINVAL: unknown lattice, N < 2, square with Lx or Ly odd and > 1 (must be
+ * bipartite), t <= 0,
  * U < 0, beta <= 0, dtau <= 0, beta/dtau not an integer to 1e-9 relative,
  * L_tau % n_wrap != 0, n_wrap < 1, N > 1024, out == NULL. *out is NULL on failure. */
-nmc_status nmc_create(int Lx, int Ly, double t, double U, double beta, double dtau,
-                      int n_wrap, uint64_t seed, nmc_ctx** out);
+nmc_status nmc_create(int lattice, int Lx, int Ly, double t, double U, double beta,
+                      double dtau, int n_wrap, uint64_t seed, nmc_ctx** out);
 
 /* Set options (copied). Allowed before the first nmc_set_fields / nmc_generate only
  * (NMC_ESTATE after). opts == NULL restores the defaults. Allocates device memory:
@@ -151,8 +164,8 @@ nmc_status nmc_sync(nmc_ctx* ctx);
 /* Host only: device bytes nmc_configure allocates for this problem and these options
  * (opts NULL = defaults), excluding the growable measurement series (8 doubles per chain
  * per measured sweep). For admission control. */
-nmc_status nmc_footprint(int Lx, int Ly, double t, double U, double beta, double dtau,
-                         int n_wrap, const nmc_options* opts, size_t* bytes);
+nmc_status nmc_footprint(int lattice, int Lx, int Ly, double t, double U, double beta,
+                         double dtau, int n_wrap, const nmc_options* opts, size_t* bytes);
 
 /* One sweep that applies the given accept decisions instead of its own
  * (uint8 [n_chains][L_tau][N], nonzero = flip; n = element count). The library still
@@ -182,9 +195,10 @@ nmc_status nmc_get_dims(const nmc_ctx* ctx, int* N, int* L_tau, int* n_chains, i
 nmc_status nmc_checkpoint(nmc_ctx* ctx, void* buf, size_t* n);
 nmc_status nmc_restore(nmc_ctx* ctx, const void* buf, size_t n);
 
-/* Host-only helper (no GPU needed): e^{c K} for the periodic Lx x Ly hopping matrix K
- * (K_ij = -t on nearest neighbours), by the library's Jacobi eigensolver. out: N x N. */
-nmc_status nmc_expk(int Lx, int Ly, double t, double c, double* out);
+/* Host-only helper (no GPU needed): e^{c K} for the hopping matrix K of an nmc_lattice
+ * (K_ij = -t on nearest neighbours), by the library's Jacobi eigensolver. out: N x N.
+ * NMC_EINVAL for the sizes nmc_create rejects. */
+nmc_status nmc_expk(int lattice, int Lx, int Ly, double t, double c, double* out);
 
 /* Host-only helper: Philox4x32-10 block function; out[4] = words of counter
  * (c0,c1,c2,c3) under key (k0,k1). Same code as the device generator's host twin. */

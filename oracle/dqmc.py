@@ -17,7 +17,10 @@ Paper passages (arXiv 2106.00712):
 
 Readings where the paper is silent (the same readings bind the CUDA library):
 R1 lattice: square, periodic; K_ij = -t for each nearest-neighbour pair, set (not summed),
-   so a length-2 direction has one bond and a length-1 direction none.
+   so a length-2 direction has one bond and a length-1 direction none. The honeycomb
+   lattice of the paper's Hubbard runs ("Models"; SM Sec. II.1: L x L cells, 2 sites per
+   cell) is the option lattice="honeycomb": site i = 2 (x + Lx y) + sub, A(x,y) bonded to
+   B(x,y), B(x-1,y), B(x,y-1) (periodic), sublattice sign +1 (A), -1 (B).
 R2 B order: B_l = e^{-dtau K} e^{V_l}, V_l = sigma*lam*diag(s(.,l)), lam = acosh(e^{dtau U/2}).
    The paper writes e^{V} e^{-dtau T}; the two cyclic products are similar matrices, so the
    weight and every flip ratio are unchanged.
@@ -59,10 +62,11 @@ class Model:
     dtau: float
     n_wrap: int
     seed: int = 0
+    lattice: str = "square"
 
     @property
     def N(self):
-        return self.Lx * self.Ly
+        return self.Lx * self.Ly * (2 if self.lattice == "honeycomb" else 1)
 
     @property
     def L_tau(self):
@@ -92,6 +96,26 @@ def hopping_matrix(Lx, Ly, t):
     return K
 
 
+def honeycomb_hopping(Lx, Ly, t):
+    """Kinetic matrix of Eq. 3 on the periodic honeycomb lattice of Lx x Ly cells (reading R1):
+    A(x,y) - B(x,y), A(x,y) - B(x-1,y), A(x,y) - B(x,y-1); set, not accumulated."""
+    N = 2 * Lx * Ly
+    K = np.zeros((N, N))
+    for y in range(Ly):
+        for x in range(Lx):
+            a = 2 * (x + Lx * y)
+            for (bx, by) in ((x, y), ((x - 1) % Lx, y), (x, (y - 1) % Ly)):
+                b = 2 * (bx + Lx * by) + 1
+                K[a, b] = K[b, a] = -t
+    return K
+
+
+def lattice_hopping(model):
+    if model.lattice == "honeycomb":
+        return honeycomb_hopping(model.Lx, model.Ly, model.t)
+    return hopping_matrix(model.Lx, model.Ly, model.t)
+
+
 def expm_sym(K, c):
     """e^{cK} for symmetric K by its eigendecomposition."""
     w, V = np.linalg.eigh(K)
@@ -107,7 +131,7 @@ class Propagators:
     """e^{-dtau K}, e^{+dtau K}, e^{-dtau K/2}, e^{+dtau K/2} for one lattice."""
 
     def __init__(self, model):
-        self.K = hopping_matrix(model.Lx, model.Ly, model.t)
+        self.K = lattice_hopping(model)
         self.expK_m = expm_sym(self.K, -model.dtau)
         self.expK_p = expm_sym(self.K, +model.dtau)
         self.expK_mh = expm_sym(self.K, -model.dtau / 2)
@@ -235,8 +259,12 @@ def green_scratch(P, fields, sigma, l, n_wrap):
 
 # ----------------------------------------------------------------------------- measure
 
-def staggered_signs(Lx, Ly):
-    """p_i = (-1)^{x_i + y_i} = e^{-i (pi,pi) . r_i}."""
+def staggered_signs(Lx, Ly, lattice="square"):
+    """Square: p_i = (-1)^{x_i + y_i} = e^{-i (pi,pi) . r_i}. Honeycomb: the sublattice sign
+    (+1 on A, -1 on B), the antiferromagnetic pattern whose structure factor the paper calls
+    S(Gamma)."""
+    if lattice == "honeycomb":
+        return np.array([1.0 if i % 2 == 0 else -1.0 for i in range(2 * Lx * Ly)])
     return np.array([(-1.0) ** (x + y) for y in range(Ly) for x in range(Lx)])
 
 
@@ -257,7 +285,7 @@ def measure(P, model, G_up, G_dn):
     epot = model.U * np.sum((0.5 - du) * (0.5 - dd)) / N
     docc = np.sum((1.0 - du) * (1.0 - dd)) / N
     dens = np.sum((1.0 - du) + (1.0 - dd)) / N
-    p = staggered_signs(model.Lx, model.Ly)
+    p = staggered_signs(model.Lx, model.Ly, model.lattice)
     eye = np.eye(N)
     nn = {}
     for a, sa in enumerate(SIGMAS):

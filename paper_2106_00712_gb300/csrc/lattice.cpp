@@ -1,15 +1,32 @@
-// Host-side lattice set-up: hopping matrix of Eq. 3 on the periodic square lattice and
+// Host-side lattice set-up: hopping matrix of Eq. 3 on the periodic square or honeycomb lattice and
 // e^{cK} by a cyclic Jacobi eigensolver (no LAPACK in the build).
 #include <cmath>
 #include <vector>
 
 namespace nmc_host {
 
-// K_ij = -t for nearest neighbours of the periodic Lx x Ly lattice, i = x + Lx*y.
-// A pair is set once, so a length-2 direction has one bond and a length-1 none.
-void hopping(int Lx, int Ly, double t, std::vector<double>& K) {
-  const int N = Lx * Ly;
+// K_ij = -t for nearest neighbours, set once per pair (so a length-2 direction has one bond
+// and a length-1 direction none).
+// lattice 0: periodic Lx x Ly square lattice, i = x + Lx*y.
+// lattice 1: periodic honeycomb of Lx x Ly cells with two sites each, i = 2 (x + Lx*y) + sub;
+//            the A site (sub 0) of cell (x,y) bonds to the B sites (sub 1) of cells (x,y),
+//            (x-1,y) and (x,y-1).
+void hopping(int lattice, int Lx, int Ly, double t, std::vector<double>& K) {
+  const int N = Lx * Ly * (lattice == 1 ? 2 : 1);
   K.assign((size_t)N * N, 0.0);
+  if (lattice == 1) {
+    for (int y = 0; y < Ly; ++y)
+      for (int x = 0; x < Lx; ++x) {
+        const int a = 2 * (x + Lx * y);
+        const int bx[3] = {x, (x + Lx - 1) % Lx, x}, by[3] = {y, y, (y + Ly - 1) % Ly};
+        for (int d = 0; d < 3; ++d) {
+          const int b = 2 * (bx[d] + Lx * by[d]) + 1;
+          K[(size_t)a * N + b] = -t;
+          K[(size_t)b * N + a] = -t;
+        }
+      }
+    return;
+  }
   const int dx[4] = {1, -1, 0, 0}, dy[4] = {0, 0, 1, -1};
   for (int y = 0; y < Ly; ++y)
     for (int x = 0; x < Lx; ++x) {

@@ -83,15 +83,14 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 //  docc  = (1/N) sum_i (1 - G~up_ii)(1 - G~dn_ii)
 //  dens  = (1/N) sum_i (2 - G~up_ii - G~dn_ii)
 //  S     = (1/4N) [ (sum_i p_i m_i)^2 + sum_sigma sum_ij p_i p_j (delta_ij - G~_ji) G~_ij ],
-//          m_i = G~dn_ii - G~up_ii, p_i = (-1)^{x_i + y_i}
+//          m_i = G~dn_ii - G~up_ii, p_i = +-1 the sublattice sign (site_parity)
 // With ns = 1 only G~up is stored and G~dn_ij = delta_ij - p_i p_j G~up_ji.
 __global__ void __launch_bounds__(kMeasThreads)
 k_measure(const double* __restrict__ Gt, const double* __restrict__ K,
-          const double* __restrict__ sign, int Lx, int Ly, double U, int ns,
+          const double* __restrict__ sign, int N, int Lx, int lattice, double U, int ns,
           double* __restrict__ acc) {
   __shared__ double red[kMeasThreads / 32];
   const int c = blockIdx.x;
-  const int N = Lx * Ly;
   const long long NN = (long long)N * N;
   const double* Gu = Gt + (long long)c * ns * NN;
   const double* Gd = Gu + NN;  // only read when ns == 2
@@ -99,7 +98,7 @@ k_measure(const double* __restrict__ Gt, const double* __restrict__ K,
   for (int e = threadIdx.x; e < (int)NN; e += blockDim.x) {
     const int i = e / N, j = e - i * N;
     const int ji = j * N + i;
-    const double pij = (((i % Lx) + (i / Lx) + (j % Lx) + (j / Lx)) & 1) ? -1.0 : 1.0;
+    const double pij = ((site_parity(i, Lx, lattice) ^ site_parity(j, Lx, lattice)) & 1) ? -1.0 : 1.0;
     const double dij = (i == j) ? 1.0 : 0.0;
     const double gu_ij = Gu[e], gu_ji = Gu[ji];
     const double gd_ij = ns == 2 ? Gd[e] : dij - pij * gu_ji;
@@ -114,7 +113,7 @@ k_measure(const double* __restrict__ Gt, const double* __restrict__ K,
     epot += (0.5 - gu) * (0.5 - gd);
     docc += (1.0 - gu) * (1.0 - gd);
     dens += 2.0 - gu - gd;
-    const double p = (((i % Lx) + (i / Lx)) & 1) ? -1.0 : 1.0;
+    const double p = site_parity(i, Lx, lattice) ? -1.0 : 1.0;
     stag += p * (gd - gu);
   }
   kin = block_sum(kin, red);
@@ -227,9 +226,9 @@ void fold_drift(const unsigned long long* stab, unsigned long long* cumulative,
   k_fold_drift<<<1, 256, 0, st>>>(stab, cumulative, hist, n_chains);
 }
 
-void measure(const double* Gt, const double* K, const double* sign, int Lx, int Ly, double U,
-             double* acc, int n_chains, int ns, cudaStream_t st) {
-  k_measure<<<n_chains, kMeasThreads, 0, st>>>(Gt, K, sign, Lx, Ly, U, ns, acc);
+void measure(const double* Gt, const double* K, const double* sign, int N, int Lx, int lattice,
+             double U, double* acc, int n_chains, int ns, cudaStream_t st) {
+  k_measure<<<n_chains, kMeasThreads, 0, st>>>(Gt, K, sign, N, Lx, lattice, U, ns, acc);
 }
 
 }  // namespace nmc

@@ -21,7 +21,7 @@
 #include "nmc_internal.cuh"
 
 namespace nmc_host {
-void hopping(int Lx, int Ly, double t, std::vector<double>& K);
+void hopping(int lattice, int Lx, int Ly, double t, std::vector<double>& K);
 void jacobi_eigh(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& V);
 void expk_from_eig(int n, const std::vector<double>& w, const std::vector<double>& V, double c,
                    std::vector<double>& out);
@@ -56,7 +56,7 @@ constexpr uint64_t kCkptMagic = 0x4e4d43434b505431ull;  // "NMCCKPT1"
 }  // namespace
 
 struct nmc_ctx {
-  int Lx = 0, Ly = 0, N = 0, Lt = 0, w = 0, nb = 0;
+  int lattice = NMC_SQUARE, Lx = 0, Ly = 0, N = 0, Lt = 0, w = 0, nb = 0;
   double t = 0, U = 0, beta = 0, dtau = 0, lam = 0;
   uint64_t seed = 0;
   nmc_options opt{};
@@ -613,12 +613,12 @@ void measure_now(nmc_ctx* x) {
     DfGemmArgs h = df_base(x, x->dT12, NN, x->dEmh2, 0);
     h.Cd = x->dM1;
     df_gemm(x, h, OZ_EMH, false);
-    launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), x->ns(), st); });
+    launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->N, x->Lx, x->lattice, x->U, acc, x->chains(), x->ns(), st); });
     return;
   }
   launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dEph, 0, x->dG, NN, x->dT1), st); });   // e^{dtau K/2} G
   launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dT1, NN, x->dEmh, 0, x->dM1), st); });  // ... e^{-dtau K/2}
-  launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->Lx, x->Ly, x->U, acc, x->chains(), x->ns(), st); });
+  launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->N, x->Lx, x->lattice, x->U, acc, x->chains(), x->ns(), st); });
 }
 
 void sweep_up(nmc_ctx* x, bool meas, const uint8_t* replay) {
@@ -802,12 +802,26 @@ void nmc_default_options(nmc_options* o) {
   o->gemm_impl = 0;
 }
 
-nmc_status nmc_create(int Lx, int Ly, double t, double U, double beta, double dtau, int n_wrap,
-                      uint64_t seed, nmc_ctx** out) {
+// Sites of a lattice, or 0 if the lattice and sizes are not accepted: square needs even
+// lengths (bipartite) or length 1; honeycomb is bipartite for any cell counts.
+static int lattice_sites(int lattice, int Lx, int Ly) {
+  if (Lx < 1 || Ly < 1 || Lx > 1024 || Ly > 1024) return 0;
+  int N = 0;
+  if (lattice == NMC_SQUARE) {
+    if ((Lx > 1 && Lx % 2) || (Ly > 1 && Ly % 2)) return 0;
+    N = Lx * Ly;
+  } else if (lattice == NMC_HONEYCOMB) {
+    N = 2 * Lx * Ly;
+  }
+  return (N >= 2 && N <= 1024) ? N : 0;
+}
+
+nmc_status nmc_create(int lattice, int Lx, int Ly, double t, double U, double beta, double dtau,
+                      int n_wrap, uint64_t seed, nmc_ctx** out) {
   if (!out) return NMC_EINVAL;
   *out = nullptr;
-  if (Lx < 1 || Ly < 1 || Lx * Ly < 2 || Lx * Ly > 1024) return NMC_EINVAL;
-  if ((Lx > 1 && Lx % 2) || (Ly > 1 && Ly % 2)) return NMC_EINVAL;
+  const int N = lattice_sites(lattice, Lx, Ly);
+  if (!N) return NMC_EINVAL;
   if (!(t > 0) || !(U >= 0) || !(beta > 0) || !(dtau > 0) || n_wrap < 1) return NMC_EINVAL;
   const double ratio = beta / dtau;
   const double Ltd = std::round(ratio);
@@ -816,11 +830,11 @@ nmc_status nmc_create(int Lx, int Ly, double t, double U, double beta, double dt
   if (Lt % n_wrap) return NMC_EINVAL;
   nmc_ctx* x = new (std::nothrow) nmc_ctx();
   if (!x) return NMC_ENOMEM;
-  x->Lx = Lx; x->Ly = Ly; x->N = Lx * Ly; x->Lt = Lt; x->w = n_wrap; x->nb = Lt / n_wrap;
+  x->lattice = lattice; x->Lx = Lx; x->Ly = Ly; x->N = N; x->Lt = Lt; x->w = n_wrap; x->nb = Lt / n_wrap;
   x->t = t; x->U = U; x->beta = beta; x->dtau = dtau; x->seed = seed;
   x->lam = std::acosh(std::exp(dtau * U / 2.0));
   nmc_default_options(&x->opt);
-  nmc_host::hopping(Lx, Ly, t, x->hK);
+  nmc_host::hopping(lattice, Lx, Ly, t, x->hK);
   std::vector<double> A = x->hK, wv, V;
   nmc_host::jacobi_eigh(x->N, A, wv, V);
   nmc_host::expk_from_eig(x->N, wv, V, -dtau, x->hEm);
@@ -912,11 +926,11 @@ nmc_status nmc_sync(nmc_ctx* x) {
   return check_drift(x);
 }
 
-nmc_status nmc_footprint(int Lx, int Ly, double t, double U, double beta, double dtau,
-                         int n_wrap, const nmc_options* opts, size_t* bytes) {
+nmc_status nmc_footprint(int lattice, int Lx, int Ly, double t, double U, double beta,
+                         double dtau, int n_wrap, const nmc_options* opts, size_t* bytes) {
   if (!bytes) return NMC_EINVAL;
   nmc_ctx* x = nullptr;
-  const nmc_status st = nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, 0, &x);
+  const nmc_status st = nmc_create(lattice, Lx, Ly, t, U, beta, dtau, n_wrap, 0, &x);
   if (st != NMC_OK) return st;
   nmc_options o;
   nmc_default_options(&o);
@@ -1068,12 +1082,13 @@ nmc_status nmc_get_green(nmc_ctx* x, int chain, int spin, double* G) {
                                 x->st()));
     NMC_CUDA(x, cudaStreamSynchronize(x->st()));
   }
-  if (x->ns() == 1 && spin == 1) {  // G_dn = I - P G_up^T P, p_i = (-1)^{x_i + y_i}
+  if (x->ns() == 1 && spin == 1) {  // G_dn = I - P G_up^T P, P = sublattice signs
     const int N = x->N;
     std::vector<double> up(G, G + NN);
     for (int i = 0; i < N; ++i)
       for (int j = 0; j < N; ++j) {
-        const int pij = (((i % x->Lx) + (i / x->Lx) + (j % x->Lx) + (j / x->Lx)) & 1) ? -1 : 1;
+        const int pij = (nmc::site_parity(i, x->Lx, x->lattice) ^
+                         nmc::site_parity(j, x->Lx, x->lattice)) ? -1 : 1;
         G[(size_t)i * N + j] = (i == j ? 1.0 : 0.0) - pij * up[(size_t)j * N + i];
       }
   }
@@ -1105,7 +1120,8 @@ nmc_status nmc_checkpoint(nmc_ctx* x, void* buf, size_t* n) {
   NMC_CUDA(x, cudaSetDevice(x->device));
   char* p = (char*)buf;
   const int64_t h[9] = {(int64_t)kCkptMagic, x->N, x->Lt, C, (int64_t)x->seed, x->sweep_counter,
-                        x->phase, x->n_series, x->opt.precision + 16 * x->opt.ph_symmetric};
+                        x->phase, x->n_series,
+                        x->opt.precision + 16 * x->opt.ph_symmetric + 256 * x->lattice};
   std::memcpy(p, h, hdr);
   p += hdr;
   cudaStream_t st = x->st();
@@ -1131,7 +1147,7 @@ nmc_status nmc_restore(nmc_ctx* x, const void* buf, size_t n) {
   std::memcpy(h, buf, hdr);
   const int C = x->opt.n_chains;
   if ((uint64_t)h[0] != kCkptMagic || h[1] != x->N || h[2] != x->Lt || h[3] != C ||
-      (uint64_t)h[4] != x->seed || h[8] != x->opt.precision + 16 * x->opt.ph_symmetric)
+      (uint64_t)h[4] != x->seed || h[8] != x->opt.precision + 16 * x->opt.ph_symmetric + 256 * x->lattice)
     return fail(x, NMC_EINVAL, "nmc_restore: checkpoint does not match this context");
   const size_t nf = (size_t)C * x->Lt * x->N;
   const long long ns = h[7];
@@ -1165,12 +1181,13 @@ nmc_status nmc_restore(nmc_ctx* x, const void* buf, size_t n) {
   return NMC_OK;
 }
 
-nmc_status nmc_expk(int Lx, int Ly, double t, double c, double* out) {
-  if (!out || Lx < 1 || Ly < 1 || Lx * Ly > 1024) return NMC_EINVAL;
+nmc_status nmc_expk(int lattice, int Lx, int Ly, double t, double c, double* out) {
+  const int N = lattice_sites(lattice, Lx, Ly);
+  if (!out || !N) return NMC_EINVAL;
   std::vector<double> K, w, V, E;
-  nmc_host::hopping(Lx, Ly, t, K);
-  nmc_host::jacobi_eigh(Lx * Ly, K, w, V);
-  nmc_host::expk_from_eig(Lx * Ly, w, V, c, E);
+  nmc_host::hopping(lattice, Lx, Ly, t, K);
+  nmc_host::jacobi_eigh(N, K, w, V);
+  nmc_host::expk_from_eig(N, w, V, c, E);
   std::memcpy(out, E.data(), E.size() * sizeof(double));
   return NMC_OK;
 }

@@ -7,6 +7,13 @@
 
 namespace nmc {
 
+// Sublattice of site i on a bipartite lattice (0 or 1); P = diag((-1)^parity) gives
+// P K P = -K. Square (lattice 0, i = x + Lx y): (x + y) mod 2. Honeycomb (lattice 1,
+// i = 2 (x + Lx y) + sub): sub, i.e. 1 on the B site of each cell.
+__host__ __device__ inline int site_parity(int i, int Lx, int lattice) {
+  return lattice == 1 ? (i & 1) : (((i % Lx) + (i / Lx)) & 1);
+}
+
 // ---------------------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies with the
 // published multipliers, key bumped by the Weyl constants between rounds.
@@ -175,7 +182,7 @@ void fold_drift(const unsigned long long* stab, unsigned long long* cumulative,
 // (energy, ekin, double_occ, s_pipi, density) * sign and sign into acc[chain][8].
 constexpr int kNumObs = 6;   // energy, ekin, docc, s_pipi, density, sign
 // ns = 1: only G~up is given and G~dn = I - P G~up^T P (particle-hole symmetry).
-void measure(const double* Gt, const double* K, const double* sign, int Lx, int Ly, double U,
-             double* acc, int n_chains, int ns, cudaStream_t st);
+void measure(const double* Gt, const double* K, const double* sign, int N, int Lx, int lattice,
+             double U, double* acc, int n_chains, int ns, cudaStream_t st);
 
 }  // namespace nmc

@@ -17,6 +17,8 @@ NMC_OK, NMC_EINVAL, NMC_ENOMEM, NMC_ECUDA, NMC_ENUMERIC, NMC_ETIMEOUT, NMC_ESTAT
 STATUS_NAMES = {0: "NMC_OK", 1: "NMC_EINVAL", 2: "NMC_ENOMEM", 3: "NMC_ECUDA",
                 4: "NMC_ENUMERIC", 5: "NMC_ETIMEOUT", 6: "NMC_ESTATE"}
 NMC_FP64, NMC_FP32, NMC_FP32X2 = 0, 1, 2
+NMC_SQUARE, NMC_HONEYCOMB = 0, 1
+LATTICES = {"square": NMC_SQUARE, "honeycomb": NMC_HONEYCOMB}
 
 # every symbol include/nmc.h declares
 EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_fields",
@@ -82,7 +84,7 @@ def load():
     vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     u32 = ctypes.c_uint32
     sig = {
-        "nmc_create": (i, [i, i, d, d, d, d, i, ctypes.c_uint64, P(vp)]),
+        "nmc_create": (i, [i, i, i, d, d, d, d, i, ctypes.c_uint64, P(vp)]),
         "nmc_configure": (i, [vp, P(Options)]),
         "nmc_default_options": (None, [P(Options)]),
         "nmc_set_fields": (i, [vp, vp, sz]),
@@ -92,7 +94,7 @@ def load():
         "nmc_sweep_async": (i, [vp, i, i]),
         "nmc_query": (i, [vp, P(i)]),
         "nmc_sync": (i, [vp]),
-        "nmc_footprint": (i, [i, i, d, d, d, d, i, P(Options), P(sz)]),
+        "nmc_footprint": (i, [i, i, i, d, d, d, d, i, P(Options), P(sz)]),
         "nmc_sweep_replay": (i, [vp, vp, sz, i]),
         "nmc_measure": (i, [vp, vp, P(Obs)]),
         "nmc_get_fields": (i, [vp, vp, sz]),
@@ -100,7 +102,7 @@ def load():
         "nmc_get_dims": (i, [vp, P(i), P(i), P(i), P(i)]),
         "nmc_checkpoint": (i, [vp, vp, P(sz)]),
         "nmc_restore": (i, [vp, vp, sz]),
-        "nmc_expk": (i, [i, i, d, d, vp]),
+        "nmc_expk": (i, [i, i, i, d, d, vp]),
         "nmc_philox": (None, [u32, u32, u32, u32, u32, u32, P(u32)]),
         "nmc_philox_device": (i, [vp, i, u32, u32, u32, u32, u32, vp, vp]),
         "nmc_drift_history": (i, [vp, vp, ctypes.c_longlong, P(ctypes.c_longlong)]),
@@ -131,9 +133,18 @@ def _ptr(a):
 
 # ------------------------------------------------------------------ raw entry points
 
-def nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed):
+def _lattice(lattice):
+    return LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+
+
+def n_sites(Lx, Ly, lattice=NMC_SQUARE):
+    return Lx * Ly * (2 if _lattice(lattice) == NMC_HONEYCOMB else 1)
+
+
+def nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed, lattice=NMC_SQUARE):
     ctx = ctypes.c_void_p()
-    st = load().nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed, ctypes.byref(ctx))
+    st = load().nmc_create(_lattice(lattice), Lx, Ly, t, U, beta, dtau, n_wrap, seed,
+                           ctypes.byref(ctx))
     if st != NMC_OK:
         raise NmcError(st, "nmc_create rejected its arguments")
     return ctx
@@ -180,9 +191,9 @@ def nmc_sync(ctx):
     _check(ctx, load().nmc_sync(ctx))
 
 
-def nmc_footprint(Lx, Ly, t, U, beta, dtau, n_wrap, opts=None):
+def nmc_footprint(Lx, Ly, t, U, beta, dtau, n_wrap, opts=None, lattice=NMC_SQUARE):
     n = ctypes.c_size_t(0)
-    st = load().nmc_footprint(Lx, Ly, t, U, beta, dtau, n_wrap,
+    st = load().nmc_footprint(_lattice(lattice), Lx, Ly, t, U, beta, dtau, n_wrap,
                               ctypes.byref(opts) if opts is not None else None, ctypes.byref(n))
     if st != NMC_OK:
         raise NmcError(st, "nmc_footprint")
@@ -236,9 +247,10 @@ def nmc_restore(ctx, blob):
     _check(ctx, load().nmc_restore(ctx, _ptr(buf), buf.size))
 
 
-def nmc_expk(Lx, Ly, t, c):
-    out = np.empty((Lx * Ly, Lx * Ly), dtype=np.float64)
-    st = load().nmc_expk(Lx, Ly, t, c, _ptr(out))
+def nmc_expk(Lx, Ly, t, c, lattice=NMC_SQUARE):
+    N = n_sites(Lx, Ly, lattice)
+    out = np.empty((N, N), dtype=np.float64)
+    st = load().nmc_expk(_lattice(lattice), Lx, Ly, t, c, _ptr(out))
     if st != NMC_OK:
         raise NmcError(st, "nmc_expk")
     return out
@@ -305,8 +317,8 @@ class Context:
 
     def __init__(self, Lx, Ly, t, U, beta, dtau, n_wrap, seed=0, n_chains=1, delay_k=16,
                  precision=NMC_FP64, drift_tol=0.0, chain_offset=0, stream=None,
-                 ph_symmetric=0, gemm_impl=0):
-        self.ctx = nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed)
+                 ph_symmetric=0, gemm_impl=0, lattice=NMC_SQUARE):
+        self.ctx = nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed, lattice)
         o = nmc_default_options()
         o.n_chains, o.delay_k, o.precision = n_chains, delay_k, precision
         o.drift_tol, o.chain_offset = drift_tol, chain_offset

@@ -36,7 +36,7 @@ def _rel(a, b):
 
 def _ctx(nmc, model, **kw):
     return nmc.Context(model.Lx, model.Ly, model.t, model.U, model.beta, model.dtau,
-                       model.n_wrap, seed=model.seed, **kw)
+                       model.n_wrap, seed=model.seed, lattice=model.lattice, **kw)
 
 
 def _compare_run(nmc, model, chains, n_sweeps, measure_from=0, delay_k=16, fields=None,
@@ -319,6 +319,23 @@ def test_ph_single_spin_8x8_256_chains_sampled(nmc):
     model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=0)
     _compare_run(nmc, model, chains=256, n_sweeps=2, measure_from=0, delay_k=16,
                  check_chains=[0, 255], precision=nmc.NMC_FP32X2, g_rel=G_REL_X2, ph=1)
+
+
+# honeycomb lattice of the paper's Hubbard runs (2 L^2 sites; U = 3.83, beta = 6, dtau = 0.1
+# at L = 6); decisions bit-exact in every mode, spin-down G derived by the sublattice signs
+@pytest.mark.parametrize("prec,ph", [(0, 0), (2, 0), (0, 1), (2, 1)])
+def test_honeycomb_matches_oracle(nmc, prec, ph):
+    model = Model(3, 3, 1.0, 3.83, 2.0, 0.1, 10, seed=5, lattice="honeycomb")
+    _compare_run(nmc, model, chains=3, n_sweeps=8, measure_from=2, delay_k=5, precision=prec,
+                 g_rel=G_REL if prec == 0 else G_REL_X2, ph=ph)
+
+
+@pytest.mark.parametrize("prec,ph", [(0, 0), (2, 1)])
+def test_honeycomb_6x6_paper_point_sampled(nmc, prec, ph):
+    model = Model(6, 6, 1.0, 3.83, 6.0, 0.1, 10, seed=0x6C, lattice="honeycomb")
+    _compare_run(nmc, model, chains=64, n_sweeps=3, measure_from=1, delay_k=16,
+                 check_chains=[1, 62], precision=prec,
+                 g_rel=G_REL if prec == 0 else G_REL_X2, ph=ph)
 
 
 def test_state_errors_on_device(nmc):

@@ -46,6 +46,15 @@ def test_create_validates_arguments(nmc):
     # 1 x 2 chain and the 2-site dimer are allowed
     for lx, ly in ((2, 1), (1, 2)):
         nmc.nmc_destroy(nmc.nmc_create(**{**good, "Lx": lx, "Ly": ly}))
+    # honeycomb: 2 sites per cell, any cell counts (bipartite by construction)
+    for lx, ly, n in ((3, 3, 18), (6, 6, 72), (1, 1, 2)):
+        ctx = nmc.nmc_create(**{**good, "Lx": lx, "Ly": ly, "lattice": nmc.NMC_HONEYCOMB})
+        assert nmc.nmc_get_dims(ctx)[0] == n
+        nmc.nmc_destroy(ctx)
+    for b in (dict(lattice=2), dict(lattice=-1), dict(lattice=nmc.NMC_HONEYCOMB, Lx=32, Ly=17)):
+        with pytest.raises(nmc.NmcError) as e:
+            nmc.nmc_create(**{**good, **b})
+        assert e.value.status == nmc.NMC_EINVAL, b
 
 
 def test_state_errors_without_gpu_work(nmc):
@@ -88,6 +97,15 @@ def test_host_expk_equals_oracle(nmc, Lx, Ly):
         ref = dqmc.expm_sym(dqmc.hopping_matrix(Lx, Ly, 1.0), c)
         # two eigensolvers: agreement to a few N * eps
         assert np.max(np.abs(mine - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("Lx,Ly", [(3, 3), (6, 6), (2, 1), (4, 2)])
+def test_host_honeycomb_expk_equals_oracle(nmc, Lx, Ly):
+    model = dqmc.Model(Lx, Ly, 1.0, 0.0, 1.0, 0.1, 10, lattice="honeycomb")
+    K = dqmc.lattice_hopping(model)
+    for c in (-0.1, 0.05):
+        mine = nmc.nmc_expk(Lx, Ly, 1.0, c, lattice="honeycomb")
+        assert np.max(np.abs(mine - dqmc.expm_sym(K, c))) < 1e-13
 
 
 def test_expk_plane_wave_closed_form(nmc):

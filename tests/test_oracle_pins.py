@@ -92,6 +92,32 @@ def test_hopping_matrix_spectrum_and_bonds():
     assert np.array_equal(Kp, ref)
 
 
+def _honeycomb_bloch_energies(Lx, Ly, t):
+    """+-t |1 + e^{i k1} + e^{i k2}|, k_a = 2 pi n_a / L_a: the two bands of the honeycomb
+    lattice (two-site cell, three bonds per A site along 0, -a1, -a2)."""
+    out = []
+    for n1 in range(Lx):
+        for n2 in range(Ly):
+            g = abs(1 + np.exp(2j * np.pi * n1 / Lx) + np.exp(2j * np.pi * n2 / Ly))
+            out += [-t * g, t * g]
+    return np.sort(out)
+
+
+@pytest.mark.parametrize("Lx,Ly", [(3, 3), (6, 6), (4, 2)])
+def test_honeycomb_hopping_spectrum_and_bonds(Lx, Ly):
+    """Honeycomb (SM Sec. II.1, 2 L^2 sites): three neighbours per site, all on the other
+    sublattice (P K P = -K), and the Bloch band energies +-t|gamma_k|."""
+    t = 0.9
+    model = Model(Lx, Ly, t, 0.0, 1.0, 0.1, 10, lattice="honeycomb")
+    K = dqmc.lattice_hopping(model)
+    assert K.shape == (2 * Lx * Ly, 2 * Lx * Ly) and np.allclose(K, K.T)
+    assert np.all((K != 0).sum(axis=1) == 3)
+    p = dqmc.staggered_signs(Lx, Ly, "honeycomb")
+    assert np.array_equal(p[:, None] * K * p[None, :], -K)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(K)), _honeycomb_bloch_energies(Lx, Ly, t),
+                       atol=1e-13)
+
+
 def test_hs_lambda_values():
     """cosh(lam) = e^{U dtau/2}; spot values for the workloads' (U, dtau)."""
     for U, dt, lam in ((4, 0.1, 0.65373), (2, 0.05, 0.31887), (4, 0.05, 0.45470),
@@ -124,7 +150,7 @@ def _enumerate(model):
     return Z, {k: v / Z for k, v in acc.items()}
 
 
-@pytest.mark.parametrize("case", ["dimer", "plaquette"])
+@pytest.mark.parametrize("case", ["dimer", "plaquette", "honeycomb_ring"])
 def test_field_sum_equals_fock_trotter(case):
     """sum_s W(s) = Tr[(e^{-dtau Hk} e^{-dtau HU})^L] and the symmetric-Trotter estimators
     equal Fock-space traces with the operator between half kinetic steps (SM Sec. I.2:
@@ -133,10 +159,17 @@ def test_field_sum_equals_fock_trotter(case):
         model = Model(2, 1, 1.0, 4.0, 1.0, 0.25, 2)
         cl = Cluster(2, DIMER_BONDS, 1.0, 4.0)
         signs = DIMER_SIGNS
-    else:
+    elif case == "plaquette":
         model = Model(2, 2, 1.0, 3.0, 0.9, 0.3, 3)
         cl = Cluster(4, PLAQ_BONDS, 1.0, 3.0)
         signs = PLAQ_SIGNS
+    else:
+        # 2 x 1 honeycomb cells: A0=0, B0=1, A1=2, B1=3; bonds A0-B0, A0-B1 (x-1), A1-B1,
+        # A1-B0 (the y-1 bond repeats the first of each cell): a four-site ring in the
+        # honeycomb site order, sublattice signs (+,-,+,-)
+        model = Model(2, 1, 1.0, 3.5, 0.8, 0.2, 2, lattice="honeycomb")
+        cl = Cluster(4, [(0, 1), (0, 3), (2, 3), (2, 1)], 1.0, 3.5)
+        signs = [1, -1, 1, -1]
     Z, obs = _enumerate(model)
     Zf = cl.z_trotter(model.dtau, model.L_tau)
     assert abs(Z / Zf - 1) < 1e-11
@@ -185,6 +218,25 @@ def test_u0_closed_form():
     assert abs(mm["energy"] - ekin) < 1e-11
     assert abs(mm["double_occ"] - 0.25) < 1e-12
     assert abs(mm["s_pipi"] - s_pipi) < 1e-11
+    assert abs(mm["density"] - 1.0) < 1e-12
+
+
+def test_u0_closed_form_honeycomb():
+    """Honeycomb, lam = 0: every flip accepted and the estimators equal sums over the Bloch
+    bands; with P K P = -K, P G P = I - G, so S(Gamma) = (1/2N) sum (1 - f)^2 too."""
+    t, beta = 1.0, 3.0
+    model = Model(3, 3, t, 0.0, beta, 0.1, 10, seed=4, lattice="honeycomb")
+    ch = Chain(model, initial_fields(model, 1), 1)
+    for _ in range(2):
+        ch.sweep(True)
+        assert ch.accepts == ch.attempts
+    eps = _honeycomb_bloch_energies(3, 3, t)
+    f = 1 / (1 + np.exp(beta * eps))
+    N = 18
+    mm = ch.means()
+    assert abs(mm["ekin"] - 2 * np.sum(eps * f) / N) < 1e-11
+    assert abs(mm["s_pipi"] - np.sum((1 - f) ** 2) / (2 * N)) < 1e-11
+    assert abs(mm["double_occ"] - 0.25) < 1e-12
     assert abs(mm["density"] - 1.0) < 1e-12
 
 
