@@ -13,6 +13,9 @@ Module map (paper = arXiv 2106.00712, Supplemental Material Sec. I.2):
   transform (SM Sec. I.2), the determinant weight and B matrices (SM Sec. I.2, last two
   equations), local Metropolis flips with determinant ratios, wraps, UDV stabilization and
   the equal-time estimators of E, double occupancy and S(pi,pi) (Eq. 4 definition of S(Q)).
+* ``nimc``     -- network initialization (Algorithm 1 steps 2-3): the generator of SM Sec. II
+  (3D transposed convolutions, sigmoid), the observable loss of Eq. 4 through the
+  determinant weight and its gradient, Adam, Bernoulli discretization of generated fields.
 
 Every algorithmic step the paper leaves open (acceptance rule, fast update, wrap, sweep
 order, stabilization, measurement cadence) follows one stated reading; each function's
