@@ -138,8 +138,10 @@ nmc_status nmc_set_fields(nmc_ctx* ctx, const int8_t* s, size_t n);
 nmc_status nmc_set_fields_device(nmc_ctx* ctx, const int8_t* d_s, size_t n);
 
 /* Generate initial fields on the device. mode 0: uniform random from Philox (tag 1),
- * ignoring `model`. Other modes (learned generators of Algorithm 1, step 3): NMC_EINVAL
- * in this library version. Then as nmc_set_fields. */
+ * ignoring `model`. mode 1: configurations from a trained generator (Algorithm 1, step 3),
+ * `model` an nmc_gen* (include/nmc_gen.h) for the same N and L_tau; chain c gets the
+ * Bernoulli fields of generation sample chain_offset + c. Other modes: NMC_EINVAL.
+ * Then as nmc_set_fields. */
 nmc_status nmc_generate(nmc_ctx* ctx, int mode, const void* model);
 
 /* Run n_sweeps sweeps on every chain (n_sweeps >= 0). Sweeps alternate direction

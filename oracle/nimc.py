@@ -30,9 +30,10 @@ N3 generated fields enter B_l = e^{-dtau K} e^{sigma lam diag x(., l)} with cont
 N4 loss: the printed sums over the batch; w1, w2 balance the two parts (the caller passes
    them; the library's training uses the inverse variances of the training targets).
 N5 generator input z: +-1 per element, -1 iff the top bit of Philox word 0 at counter
-   (element, sample, 0, tag 2) is set (tag 1's rule for initial fields).
-N6 Bernoulli: s = +1 iff u < p, u = word 0 * 2^-32 at counter (l*N + i, sample, 0, tag 3),
-   compared in double with p as given (float32 from the library's generator).
+   (element, sample, stream, tag 2) is set (tag 1's rule for initial fields); stream 0 is
+   the training set's fixed inputs, stream 1 fresh inputs for generation.
+N6 Bernoulli: s = +1 iff u < p, u = word 0 * 2^-32 at counter (l*N + i, sample, stream,
+   tag 3), compared in double with p as given (float32 from the library's generator).
 N7 Adam: Kingma & Ba's update with bias corrections and epsilon = 1e-7 (the TensorFlow
    default; the paper trains in TensorFlow and gives no epsilon).
 N8 initial weights: Glorot uniform, limit sqrt(6 / (fan_in + fan_out)) with
@@ -91,13 +92,14 @@ def fields_from_p(p):
     return (2.0 * p - 1.0).transpose(0, 1, 3, 2).reshape(B, L, A * Bd)
 
 
-def generator_input(seed, n0, count, shape):
-    """Reading N5: +-1 inputs for samples n0 .. n0+count-1, float64 [count, *shape]."""
+def generator_input(seed, n0, count, shape, stream=0):
+    """Reading N5: +-1 inputs for samples n0 .. n0+count-1 of an input stream (0 for the
+    training set, 1 for generation), float64 [count, *shape]."""
     k0, k1 = seed_key(seed)
     size = int(np.prod(shape))
     e = np.arange(size, dtype=np.uint64)[None, :]
     n = (n0 + np.arange(count, dtype=np.uint64))[:, None]
-    w0 = philox4x32_10(e, n, 0, TAG_GEN_Z, k0, k1)[0]
+    w0 = philox4x32_10(e, n, stream, TAG_GEN_Z, k0, k1)[0]
     return np.where((w0 >> np.uint64(31)) != 0, -1.0, 1.0).reshape((count,) + tuple(shape))
 
 
@@ -116,13 +118,13 @@ def glorot_params(seed, arch):
     return params
 
 
-def bernoulli_fields(seed, p_flat, n0):
+def bernoulli_fields(seed, p_flat, n0, stream=0):
     """Reading N6. p_flat: [B, L_tau, N] probabilities (as given); returns int8 +-1."""
     k0, k1 = seed_key(seed)
     B, L, N = p_flat.shape
     ctr = np.arange(L * N, dtype=np.uint64)[None, :]
     n = (n0 + np.arange(B, dtype=np.uint64))[:, None]
-    u = philox4x32_10(ctr, n, 0, TAG_BERNOULLI, k0, k1)[0].astype(np.float64) * 2.0 ** -32
+    u = philox4x32_10(ctr, n, stream, TAG_BERNOULLI, k0, k1)[0].astype(np.float64) * 2.0 ** -32
     p = np.asarray(p_flat, dtype=np.float64).reshape(B, L * N)
     return np.where(u < p, 1, -1).astype(np.int8).reshape(B, L, N)
 

@@ -18,7 +18,12 @@
 #include <vector>
 
 #include "../../include/nmc.h"
+#include "../../include/nmc_gen.h"
 #include "nmc_internal.cuh"
+
+// nimc.cu: Bernoulli fields from a generator (stream 1, samples n0..n0+n-1), synchronised
+nmc_status nmc_gen_fill_fields(nmc_gen* g, int N, int Lt, long long n0, int n, int8_t* d_fields,
+                               cudaStream_t st);
 
 namespace nmc_host {
 void hopping(int lattice, int Lx, int Ly, double t, std::vector<double>& K);
@@ -882,14 +887,22 @@ nmc_status nmc_set_fields_device(nmc_ctx* x, const int8_t* d_s, size_t n) {
 }
 
 nmc_status nmc_generate(nmc_ctx* x, int mode, const void* model) {
-  (void)model;
   if (!x) return NMC_EINVAL;
-  if (mode != 0) return fail(x, NMC_EINVAL, "nmc_generate: only mode 0 (random) is available");
+  if (mode != 0 && mode != 1) return fail(x, NMC_EINVAL, "nmc_generate: mode must be 0 or 1");
+  if (mode == 1 && !model) return fail(x, NMC_EINVAL, "nmc_generate: mode 1 needs a generator");
   NMC_TRY(ensure_configured(x));
-  launch(x, KC_OTHER, [&] {
-    init_fields(x->dS, x->chains(), x->Lt, x->N, (uint32_t)(x->seed & 0xffffffffu),
-                (uint32_t)(x->seed >> 32), x->opt.chain_offset, x->st());
-  });
+  if (mode == 1) {
+    NMC_CUDA(x, cudaStreamSynchronize(x->st()));   // the generator writes on its own stream
+    const nmc_status s = nmc_gen_fill_fields((nmc_gen*)const_cast<void*>(model), x->N, x->Lt,
+                                             x->opt.chain_offset, x->chains(), x->dS, x->st());
+    if (s != NMC_OK) return fail(x, s, std::string("nmc_generate: ") +
+                                        nmc_gen_last_error((const nmc_gen*)model));
+  } else {
+    launch(x, KC_OTHER, [&] {
+      init_fields(x->dS, x->chains(), x->Lt, x->N, (uint32_t)(x->seed & 0xffffffffu),
+                  (uint32_t)(x->seed >> 32), x->opt.chain_offset, x->st());
+    });
+  }
   NMC_CUDA(x, cudaGetLastError());
   return after_fields(x);
 }

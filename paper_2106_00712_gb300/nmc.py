@@ -64,6 +64,17 @@ class Obs(ctypes.Structure):
         return out
 
 
+class GenArch(ctypes.Structure):
+    _fields_ = [("z", ctypes.c_int * 3), ("c1", ctypes.c_int), ("k1", ctypes.c_int * 3),
+                ("k2", ctypes.c_int * 3)]
+
+
+EXPORTED_GEN = ("nmc_gen_paper_arch", "nmc_gen_create", "nmc_gen_get_params",
+                "nmc_gen_set_params", "nmc_gen_probs", "nmc_gen_sample_fields",
+                "nmc_gen_observables", "nmc_gen_loss_grad", "nmc_gen_train_step",
+                "nmc_gen_train", "nmc_gen_steps", "nmc_gen_last_error", "nmc_gen_destroy")
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_longlong),
                 ("timed", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
@@ -112,6 +123,21 @@ def load():
         "nmc_last_error": (ctypes.c_char_p, [vp]),
         "nmc_version": (ctypes.c_char_p, []),
         "nmc_destroy": (None, [vp]),
+        # include/nmc_gen.h
+        "nmc_gen_paper_arch": (None, [P(GenArch)]),
+        "nmc_gen_create": (i, [i, i, i, d, d, d, d, i, P(GenArch), ctypes.c_uint64, i, vp,
+                               P(vp)]),
+        "nmc_gen_get_params": (i, [vp, vp, vp, vp, vp]),
+        "nmc_gen_set_params": (i, [vp, vp, vp, vp, vp]),
+        "nmc_gen_probs": (i, [vp, ctypes.c_longlong, i, i, vp]),
+        "nmc_gen_sample_fields": (i, [vp, ctypes.c_longlong, i, i, vp]),
+        "nmc_gen_observables": (i, [vp, vp, i, vp]),
+        "nmc_gen_loss_grad": (i, [vp, vp, i, vp, d, d, vp, vp]),
+        "nmc_gen_train_step": (i, [vp, vp, i, vp, d, d, d, P(d)]),
+        "nmc_gen_train": (i, [vp, vp, i, i, i, d, d, d, vp]),
+        "nmc_gen_steps": (ctypes.c_longlong, [vp]),
+        "nmc_gen_last_error": (ctypes.c_char_p, [vp]),
+        "nmc_gen_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -353,8 +379,11 @@ class Context:
     def set_fields(self, s):
         nmc_set_fields(self.ctx, s)
 
-    def generate(self, mode=0):
-        nmc_generate(self.ctx, mode)
+    def generate(self, mode=0, model=None):
+        """mode 0: random fields; mode 1: Bernoulli fields from a Generator (or its handle)."""
+        if isinstance(model, Generator):
+            model = model.g
+        nmc_generate(self.ctx, mode, model)
 
     def sweep(self, n, measure=1):
         nmc_sweep(self.ctx, n, measure)
@@ -394,3 +423,116 @@ class Context:
 
     def kernel_stats(self, reset=False):
         return nmc_kernel_stats(self.ctx, reset)
+
+
+# ------------------------------------------------------------------ generator (nmc_gen.h)
+
+def gen_arch(z=None, c1=None, k1=None, k2=None):
+    """The paper's honeycomb network (SM Sec. II), with any field overridden."""
+    a = GenArch()
+    load().nmc_gen_paper_arch(ctypes.byref(a))
+    if z is not None:
+        a.z[:] = list(z)
+    if c1 is not None:
+        a.c1 = int(c1)
+    if k1 is not None:
+        a.k1[:] = list(k1)
+    if k2 is not None:
+        a.k2[:] = list(k2)
+    return a
+
+
+def _gcheck(g, status):
+    if status != NMC_OK:
+        msg = load().nmc_gen_last_error(g) if g else b""
+        raise NmcError(status, (msg or b"").decode())
+
+
+class Generator:
+    """Owning wrapper of an nmc_gen (generator network, Eq. 4 loss and training).
+    Device-pointer arguments are integers (e.g. torch ``data_ptr()``)."""
+
+    def __init__(self, Lx, Ly, t, U, beta, dtau, n_wrap, arch=None, seed=0, max_batch=64,
+                 stream=None, lattice=NMC_SQUARE):
+        self.arch = arch if arch is not None else gen_arch()
+        h = ctypes.c_void_p()
+        st = load().nmc_gen_create(_lattice(lattice), Lx, Ly, t, U, beta, dtau, n_wrap,
+                                   ctypes.byref(self.arch), seed, max_batch, stream,
+                                   ctypes.byref(h))
+        if st != NMC_OK:
+            raise NmcError(st, "nmc_gen_create rejected its arguments")
+        self.g = h
+        a = self.arch
+        self.k1 = tuple(a.k1)
+        self.k2 = tuple(a.k2)
+        self.z_shape = tuple(a.z)
+        self.c1 = a.c1
+        self.L_tau = a.z[0] + a.k1[0] + a.k2[0] - 2
+        self.A = a.z[1] + a.k1[1] + a.k2[1] - 2
+        self.B = a.z[2] + a.k1[2] + a.k2[2] - 2
+        self.N = self.A * self.B
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def close(self):
+        if self.g is not None:
+            load().nmc_gen_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        W1 = np.zeros((1, self.c1) + self.k1, dtype=np.float32)
+        b1 = np.zeros(self.c1, dtype=np.float32)
+        W2 = np.zeros((self.c1, 1) + self.k2, dtype=np.float32)
+        b2 = np.zeros(1, dtype=np.float32)
+        _gcheck(self.g, load().nmc_gen_get_params(self.g, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2)))
+        return [(W1, b1), (W2, b2)]
+
+    def set_params(self, params):
+        (W1, b1), (W2, b2) = [(np.ascontiguousarray(W, dtype=np.float32),
+                               np.ascontiguousarray(b, dtype=np.float32)) for (W, b) in params]
+        _gcheck(self.g, load().nmc_gen_set_params(self.g, _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2)))
+
+    def probs(self, n0, n, stream_id, d_p):
+        _gcheck(self.g, load().nmc_gen_probs(self.g, n0, n, stream_id, ctypes.c_void_p(d_p)))
+
+    def sample_fields(self, n0, n, stream_id, d_fields):
+        _gcheck(self.g, load().nmc_gen_sample_fields(self.g, n0, n, stream_id,
+                                                     ctypes.c_void_p(d_fields)))
+
+    def observables(self, d_x, n, d_obs):
+        _gcheck(self.g, load().nmc_gen_observables(self.g, ctypes.c_void_p(d_x), n,
+                                                   ctypes.c_void_p(d_obs)))
+
+    def loss_grad(self, d_x, n, d_targets, w1, w2, d_loss=0, d_grad=0):
+        _gcheck(self.g, load().nmc_gen_loss_grad(self.g, ctypes.c_void_p(d_x), n,
+                                                 ctypes.c_void_p(d_targets), w1, w2,
+                                                 ctypes.c_void_p(d_loss or None),
+                                                 ctypes.c_void_p(d_grad or None)))
+
+    def train_step(self, ids, targets, w1, w2, lr):
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        tg = np.ascontiguousarray(targets, dtype=np.float64)
+        out = ctypes.c_double(0)
+        _gcheck(self.g, load().nmc_gen_train_step(self.g, _ptr(ids), len(ids), _ptr(tg), w1, w2,
+                                                  lr, ctypes.byref(out)))
+        return out.value
+
+    def train(self, targets, epochs, batch, lr=1e-3, w1=0.0, w2=0.0):
+        tg = np.ascontiguousarray(targets, dtype=np.float64)
+        out = np.zeros(max(epochs, 1), dtype=np.float64)
+        _gcheck(self.g, load().nmc_gen_train(self.g, _ptr(tg), tg.shape[0], epochs, batch, lr,
+                                             w1, w2, _ptr(out)))
+        return out[:epochs]
+
+    def steps(self):
+        return load().nmc_gen_steps(self.g)

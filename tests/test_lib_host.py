@@ -32,6 +32,17 @@ def test_exports_every_declared_symbol(nmc):
     assert "sm_103a" in nmc.nmc_version()
 
 
+def test_exports_every_generator_symbol(nmc):
+    header = open(os.path.join(ROOT, "include", "nmc_gen.h")).read()
+    declared = set(re.findall(r"\b(nmc_gen_[a-z_]+)\s*\(", header))
+    assert declared == set(nmc.EXPORTED_GEN), declared ^ set(nmc.EXPORTED_GEN)
+    lib = ctypes.CDLL(nmc.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    a = nmc.gen_arch()
+    assert (tuple(a.z), a.c1, tuple(a.k1), tuple(a.k2)) == ((10, 2, 2), 20, (16, 6, 3), (36, 6, 3))
+
+
 def test_create_validates_arguments(nmc):
     good = dict(Lx=4, Ly=4, t=1.0, U=4.0, beta=2.0, dtau=0.1, n_wrap=10, seed=0)
     ctx = nmc.nmc_create(**good)
