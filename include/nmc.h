@@ -175,6 +175,13 @@ nmc_status nmc_footprint(int lattice, int Lx, int Ly, double t, double U, double
  * (nmc_obs.n_disagree). Used to compare precisions on identical trajectories. */
 nmc_status nmc_sweep_replay(nmc_ctx* ctx, const uint8_t* accept, size_t n, int measure);
 
+/* Per-sweep accumulators of the measuring sweeps since the last reset (host out, double
+ * [n][n_chains][8], n = min(max_sweeps, *n_sweeps)): for each measured sweep and chain the
+ * sums over that sweep's L_tau/n_wrap measurements of sign * (energy, ekin, double_occ,
+ * s_pipi, density), the sum of the signs, and two zeros; the sweep's estimate of an
+ * observable is entry k / entry 5. *n_sweeps receives the number recorded. */
+nmc_status nmc_series(nmc_ctx* ctx, double* out, long long max_sweeps, long long* n_sweeps);
+
 /* Reduce the accumulators. per_chain: array of n_chains (or NULL); pooled: one (or
  * NULL). Pooled means are averages of per-chain means; errors as in nmc_est. */
 nmc_status nmc_measure(nmc_ctx* ctx, nmc_obs* per_chain, nmc_obs* pooled);

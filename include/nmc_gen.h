@@ -85,6 +85,11 @@ nmc_status nmc_gen_sample_fields(nmc_gen* g, long long n0, int n, int stream,
  * values; +-1 for Markov-chain samples): d_obs (device, double [n][2]) = (S, E_k). */
 nmc_status nmc_gen_observables(nmc_gen* g, const double* d_x, int n, double* d_obs);
 
+/* Observables measured directly on generated configurations (the footnote to Algorithm 1:
+ * x = 2p - 1) for samples n0 .. n0+n-1 of `stream`: d_obs (device, double [n][2]). */
+nmc_status nmc_gen_generated_observables(nmc_gen* g, long long n0, int n, int stream,
+                                         double* d_obs);
+
 /* Eq. 4 per configuration and its exact gradient: d_targets (device, double [n][2] =
  * (S_l, E_k,l)); outputs d_loss (device, double [n], may be NULL) and d_grad (device,
  * double [n][L_tau][N], may be NULL). */

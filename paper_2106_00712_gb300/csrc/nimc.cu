@@ -765,6 +765,20 @@ nmc_status nmc_gen_observables(nmc_gen* g, const double* d_x, int n, double* d_o
   return NMC_OK;
 }
 
+nmc_status nmc_gen_generated_observables(nmc_gen* g, long long n0, int n, int stream,
+                                         double* d_obs) {
+  if (!g || n < 0 || (n > 0 && !d_obs) || n0 < 0 || stream < 0) return NMC_EINVAL;
+  const long long LN = (long long)g->Lt * g->N;
+  for (int c0 = 0; c0 < n; c0 += g->Bc) {
+    const int m = std::min(g->Bc, n - c0);
+    forward(g, nullptr, n0 + c0, m, (uint32_t)stream);
+    k_p_to_x<<<blocks_for(m * LN), kThreads, 0, g->stream>>>(g->dPo, m, g->Lt, g->A, g->B, g->dX);
+    GEN_TRY(loss_chunk(g, m, nullptr, 0, 0, d_obs + 2LL * c0, nullptr, nullptr));
+  }
+  GEN_CUDA(g, cudaStreamSynchronize(g->stream));
+  return NMC_OK;
+}
+
 nmc_status nmc_gen_loss_grad(nmc_gen* g, const double* d_x, int n, const double* d_targets,
                              double w1, double w2, double* d_loss, double* d_grad) {
   if (!g || n < 0 || (n > 0 && (!d_x || !d_targets))) return NMC_EINVAL;

@@ -968,6 +968,19 @@ nmc_status nmc_sweep_replay(nmc_ctx* x, const uint8_t* accept, size_t n, int mea
   return run_sweeps(x, 1, measure, x->dReplay);
 }
 
+nmc_status nmc_series(nmc_ctx* x, double* out, long long max_sweeps, long long* n_sweeps) {
+  if (!x || !n_sweeps || max_sweeps < 0 || (max_sweeps > 0 && !out)) return NMC_EINVAL;
+  if (!x->configured) return fail(x, NMC_ESTATE, "nmc_series before configuration");
+  NMC_CUDA(x, cudaSetDevice(x->device));
+  *n_sweeps = x->n_series;
+  const long long S = std::min(max_sweeps, x->n_series);
+  if (S > 0)
+    NMC_CUDA(x, cudaMemcpyAsync(out, x->dSeries, (size_t)S * x->chains() * 8 * sizeof(double),
+                                cudaMemcpyDeviceToHost, x->st()));
+  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  return NMC_OK;
+}
+
 nmc_status nmc_measure(nmc_ctx* x, nmc_obs* per_chain, nmc_obs* pooled) {
   if (!x) return NMC_EINVAL;
   if (!x->configured) return fail(x, NMC_ESTATE, "nmc_measure before configuration");

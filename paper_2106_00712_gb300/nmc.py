@@ -25,7 +25,7 @@ EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_field
             "nmc_set_fields_device", "nmc_generate", "nmc_sweep", "nmc_sweep_async",
             "nmc_query", "nmc_sync", "nmc_footprint", "nmc_sweep_replay",
             "nmc_measure", "nmc_get_fields", "nmc_get_green", "nmc_get_dims",
-            "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_philox", "nmc_philox_device",
+            "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_series", "nmc_philox", "nmc_philox_device",
             "nmc_drift_history", "nmc_profile", "nmc_kernel_stats", "nmc_green_noalloc",
             "nmc_last_error",
             "nmc_version", "nmc_destroy")
@@ -71,7 +71,8 @@ class GenArch(ctypes.Structure):
 
 EXPORTED_GEN = ("nmc_gen_paper_arch", "nmc_gen_create", "nmc_gen_get_params",
                 "nmc_gen_set_params", "nmc_gen_probs", "nmc_gen_sample_fields",
-                "nmc_gen_observables", "nmc_gen_loss_grad", "nmc_gen_train_step",
+                "nmc_gen_observables", "nmc_gen_generated_observables",
+                "nmc_gen_loss_grad", "nmc_gen_train_step",
                 "nmc_gen_train", "nmc_gen_steps", "nmc_gen_last_error", "nmc_gen_destroy")
 
 
@@ -108,6 +109,7 @@ def load():
         "nmc_footprint": (i, [i, i, i, d, d, d, d, i, P(Options), P(sz)]),
         "nmc_sweep_replay": (i, [vp, vp, sz, i]),
         "nmc_measure": (i, [vp, vp, P(Obs)]),
+        "nmc_series": (i, [vp, vp, ctypes.c_longlong, P(ctypes.c_longlong)]),
         "nmc_get_fields": (i, [vp, vp, sz]),
         "nmc_get_green": (i, [vp, i, i, vp]),
         "nmc_get_dims": (i, [vp, P(i), P(i), P(i), P(i)]),
@@ -133,6 +135,7 @@ def load():
         "nmc_gen_sample_fields": (i, [vp, ctypes.c_longlong, i, i, vp]),
         "nmc_gen_observables": (i, [vp, vp, i, vp]),
         "nmc_gen_loss_grad": (i, [vp, vp, i, vp, d, d, vp, vp]),
+        "nmc_gen_generated_observables": (i, [vp, ctypes.c_longlong, i, i, vp]),
         "nmc_gen_train_step": (i, [vp, vp, i, vp, d, d, d, P(d)]),
         "nmc_gen_train": (i, [vp, vp, i, i, i, d, d, d, vp]),
         "nmc_gen_steps": (ctypes.c_longlong, [vp]),
@@ -282,6 +285,18 @@ def nmc_expk(Lx, Ly, t, c, lattice=NMC_SQUARE):
     return out
 
 
+def nmc_series(ctx):
+    """Per measured sweep and chain: (energy, ekin, double_occ, s_pipi, density) estimates,
+    float64 [n_sweeps][n_chains][5] (sign-weighted sums over the sweep / sum of signs)."""
+    n = ctypes.c_longlong(0)
+    _check(ctx, load().nmc_series(ctx, None, 0, ctypes.byref(n)))
+    C = nmc_get_dims(ctx)[2]
+    buf = np.zeros((max(n.value, 1), C, 8), dtype=np.float64)
+    _check(ctx, load().nmc_series(ctx, _ptr(buf), n.value, ctypes.byref(n)))
+    buf = buf[:n.value]
+    return buf[:, :, :5] / buf[:, :, 5:6]
+
+
 def nmc_philox(c0, c1, c2, c3, k0, k1):
     out = (ctypes.c_uint32 * 4)()
     load().nmc_philox(c0, c1, c2, c3, k0, k1, out)
@@ -403,6 +418,9 @@ class Context:
     def measure(self, per_chain=False):
         return nmc_measure(self.ctx, per_chain)
 
+    def series(self):
+        return nmc_series(self.ctx)
+
     def fields(self):
         return nmc_get_fields(self.ctx)
 
@@ -512,6 +530,10 @@ class Generator:
     def observables(self, d_x, n, d_obs):
         _gcheck(self.g, load().nmc_gen_observables(self.g, ctypes.c_void_p(d_x), n,
                                                    ctypes.c_void_p(d_obs)))
+
+    def generated_observables(self, n0, n, stream_id, d_obs):
+        _gcheck(self.g, load().nmc_gen_generated_observables(self.g, n0, n, stream_id,
+                                                             ctypes.c_void_p(d_obs)))
 
     def loss_grad(self, d_x, n, d_targets, w1, w2, d_loss=0, d_grad=0):
         _gcheck(self.g, load().nmc_gen_loss_grad(self.g, ctypes.c_void_p(d_x), n,

@@ -191,3 +191,35 @@ def test_training_reduces_the_loss(env):
         hist = g.train(tg, epochs=10, batch=4, lr=2e-2)
         assert g.steps() == 10 * 6
     assert np.all(np.isfinite(hist)) and hist[-1] < 0.9 * hist[0], hist
+
+
+def test_generated_observables_match_oracle(env):
+    torch, nmc = env
+    m = Model(3, 3, 1.0, 3.83, 1.0, 0.1, 5, lattice="honeycomb")
+    with _gen(nmc, m, arch=_arch_for(m), seed=21, max_batch=2) as g:
+        n = 3
+        d_p = torch.empty((n, m.L_tau, 6, 3), dtype=torch.float32, device="cuda")
+        g.probs(5, n, 1, d_p.data_ptr())
+        d_o = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+        g.generated_observables(5, n, 1, d_o.data_ptr())
+        x = nimc.fields_from_p(d_p.cpu().numpy().astype(np.float64))
+        got = d_o.cpu().numpy()
+    for b in range(n):
+        ek, s = nimc.observables(m, x[b])
+        assert abs(got[b, 0] - s) < 1e-10 and abs(got[b, 1] - ek) < 1e-10
+
+
+def test_series_is_consistent_with_measure(env):
+    torch, nmc = env
+    m = Model(3, 3, 1.0, 3.83, 2.0, 0.1, 5, seed=3, lattice="honeycomb")
+    with nmc.Context(m.Lx, m.Ly, m.t, m.U, m.beta, m.dtau, m.n_wrap, seed=m.seed, n_chains=4,
+                     lattice=m.lattice) as c:
+        c.generate()
+        c.sweep(2, measure=0)
+        c.sweep(5, measure=1)
+        ser = c.series()
+        _, per = c.measure(per_chain=True)
+    assert ser.shape == (5, 4, 5)
+    for ch in range(4):
+        for k, name in enumerate(("energy", "ekin", "double_occ", "s_pipi", "density")):
+            assert abs(ser[:, ch, k].mean() - getattr(per[ch], name).mean) < 1e-12
