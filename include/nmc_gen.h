@@ -104,11 +104,21 @@ nmc_status nmc_gen_train_step(nmc_gen* g, const long long* ids, int n, const dou
 
 /* Train on n samples (targets host [n][2], sample k paired with input z(k, 0)) for
  * `epochs` passes in a random order (Fisher-Yates with Philox uniforms at counter
- * (k, epoch, 0, 5)), `batch` samples per step (last step of an epoch may be smaller).
+ * (k, epoch, 0, 5), epoch counted since creation or the last nmc_gen_set_params, so that
+ * successive calls continue one schedule), `batch` samples per step (the last step of an
+ * epoch may be smaller). NMC_ENUMERIC if a configuration's density departs from 1 by
+ * more than 1e-6 (a failed stabilization; the message names the batch), before the
+ * update of that step.
  * w1, w2 <= 0 select the inverse variances of the targets. epoch_loss (host, may be NULL):
  * mean loss per sample of each epoch. */
 nmc_status nmc_gen_train(nmc_gen* g, const double* targets, int n, int epochs, int batch,
                          double lr, double w1, double w2, double* epoch_loss);
+
+/* Bound the global norm of each step's gradient (over all parameters) by max_norm before
+ * the Adam update (0, the default: no bound; the paper states none). Single-configuration
+ * estimators are unbounded, and a generator driven into saturation meets configurations
+ * whose loss gradient is many orders above the typical one. */
+nmc_status nmc_gen_set_clip(nmc_gen* g, double max_norm);
 
 /* Adam steps taken since creation or the last nmc_gen_set_params. */
 long long nmc_gen_steps(const nmc_gen* g);

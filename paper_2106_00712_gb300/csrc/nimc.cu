@@ -166,10 +166,29 @@ __global__ void k_gen_input(const long long* __restrict__ ids, long long n0, int
   }
 }
 
+// scale[0] = min(1, max_norm / |g|) (1 when max_norm <= 0); one CTA
+__global__ void k_clip_scale(const float* __restrict__ g, int n, float max_norm,
+                             float* __restrict__ scale) {
+  __shared__ double red[kThreads / 32];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) s += (double)g[e] * g[e];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+    const double nrm = sqrt(t);
+    scale[0] = (max_norm > 0.f && nrm > max_norm) ? (float)(max_norm / nrm) : 1.f;
+  }
+}
+
 __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, int n, float lr, float c1, float c2) {
+                       float* __restrict__ v, int n, float lr, float c1, float c2,
+                       const float* __restrict__ scale) {
+  const float sc = scale[0];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const float gi = g[e];
+    const float gi = g[e] * sc;
     const float mi = (float)kAdamB1 * m[e] + (1.f - (float)kAdamB1) * gi;
     const float vi = (float)kAdamB2 * v[e] + (1.f - (float)kAdamB2) * gi * gi;
     m[e] = mi;
@@ -253,7 +272,7 @@ __global__ void k_loss_gbar(const double* __restrict__ Gt, const double* __restr
                             const double* __restrict__ targets, double w1, double w2,
                             const double* __restrict__ K, int N, int Lx, int lattice,
                             double* __restrict__ Gbt, double* __restrict__ loss,
-                            double* __restrict__ obs) {
+                            double* __restrict__ obs, int* __restrict__ bad) {
   __shared__ double red[kThreads / 32];
   const int c = blockIdx.x;
   const long long NN = (long long)N * N;
@@ -267,6 +286,12 @@ __global__ void k_loss_gbar(const double* __restrict__ Gt, const double* __restr
   }
   stag = block_sum(stag, red);
   if (threadIdx.x == 0) {
+    // health check: at half filling on a bipartite lattice the density is 1 for any real
+    // field (G_dn = I - P G_up^T P), so a departure flags a failed stabilization
+    // (the estimators of a single field configuration are not bounded by the physical
+    // ranges, so only the density and finiteness are checked)
+    const double dens = acc[c * 8 + 4];
+    if (!(fabs(dens - 1.0) <= 1e-6) || !isfinite(s) || !isfinite(ek)) atomicMax(bad, c + 1);
     if (obs) { obs[2 * c] = s; obs[2 * c + 1] = ek; }
     if (loss) {
       const double dS = s - targets[2 * c], dE = ek - targets[2 * c + 1];
@@ -333,6 +358,9 @@ struct nmc_gen {
   int device = 0;
   cudaStream_t stream = nullptr;
   long long steps = 0;
+  long long epochs = 0;   // epochs trained since creation / set_params (shuffle counter)
+  double clip = 0.0;      // global gradient-norm bound (0: none)
+  float* dScale = nullptr;
   std::string err;
   std::vector<void*> allocs;
   // parameters [W1 | b1 | W2 | b2], gradients, Adam moments (float32)
@@ -352,6 +380,7 @@ struct nmc_gen {
   double *dGl = nullptr, *dGl2 = nullptr, *dH = nullptr, *dH2 = nullptr;
   double *dG0 = nullptr, *dGt = nullptr, *dGbt = nullptr, *dGbar = nullptr, *dQ = nullptr;
   double *dAcc = nullptr, *dSign = nullptr, *dTarg = nullptr, *dLoss = nullptr, *dGx = nullptr;
+  int* dBad = nullptr;
 
   long long NN() const { return (long long)N * N; }
   float* W1() const { return dP; }
@@ -514,12 +543,26 @@ nmc_status loss_chunk(nmc_gen* g, int n, const double* targets, double w1, doubl
   gemm(gbase(g, nb2, g->dEph, 0, g->dG0, NN, g->dT1), st);
   gemm(gbase(g, nb2, g->dT1, NN, g->dEmh, 0, g->dGt), st);
   k_fill<<<blocks_for(8LL * n), kThreads, 0, st>>>(g->dAcc, 8LL * n, 0.0);
+  GEN_CUDA(g, cudaMemsetAsync(g->dBad, 0, sizeof(int), st));
   measure(g->dGt, g->dK, g->dSign, g->N, g->Lx, g->lattice, g->U, g->dAcc, n, 2, st);
   const bool want_grad = grad != nullptr;
   k_loss_gbar<<<n, kThreads, 0, st>>>(g->dGt, g->dAcc, targets, w1, w2, g->dK, g->N, g->Lx,
                                       g->lattice, want_grad ? g->dGbt : nullptr,
-                                      targets ? loss : nullptr, obs);
+                                      targets ? loss : nullptr, obs, g->dBad);
   GEN_CUDA(g, cudaGetLastError());
+  {
+    int bad = 0;
+    GEN_CUDA(g, cudaMemcpyAsync(&bad, g->dBad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GEN_CUDA(g, cudaStreamSynchronize(st));
+    if (bad) {
+      double a[8];
+      GEN_CUDA(g, cudaMemcpy(a, g->dAcc + 8LL * (bad - 1), sizeof a, cudaMemcpyDeviceToHost));
+      char buf[200];
+      std::snprintf(buf, sizeof buf, "configuration %d of the chunk: density %.3e, S %.3e, E_k %.3e "
+                    "(stabilization failed)", bad - 1, a[4], a[3], a[1]);
+      return gfail(g, NMC_ENUMERIC, buf);
+    }
+  }
   if (!want_grad) return NMC_OK;
   gemm(gbase(g, nb2, g->dEph, 0, g->dGbt, NN, g->dT1), st);
   gemm(gbase(g, nb2, g->dT1, NN, g->dEmh, 0, g->dGbar), st);
@@ -659,6 +702,8 @@ nmc_status nmc_gen_create(int lattice, int Lx, int Ly, double t, double U, doubl
   A_(g->dWS, 2 * M2 * NN);
   A_(g->dAcc, 8LL * g->Bc); A_(g->dSign, g->Bc); A_(g->dTarg, 2LL * g->Bf);
   A_(g->dLoss, g->Bf); A_(g->dGx, (long long)g->Bc * LN);
+  A_(g->dBad, 1);
+  A_(g->dScale, 1);
   if (s != NMC_OK) return bail(s);
 
   std::vector<double> I(NN, 0.0), ones(std::max<long long>(N, g->Bc), 1.0);
@@ -720,6 +765,7 @@ nmc_status nmc_gen_set_params(nmc_gen* g, const float* W1, const float* b1, cons
   GEN_CUDA(g, cudaMemset(g->dM, 0, g->nP * sizeof(float)));
   GEN_CUDA(g, cudaMemset(g->dV, 0, g->nP * sizeof(float)));
   g->steps = 0;
+  g->epochs = 0;
   return NMC_OK;
 }
 
@@ -811,7 +857,14 @@ nmc_status nmc_gen_train_step(nmc_gen* g, const long long* ids, int n, const dou
                                 cudaMemcpyHostToDevice, st));
     forward(g, g->dIds, 0, m, 0u);
     k_p_to_x<<<blocks_for(m * LN), kThreads, 0, st>>>(g->dPo, m, g->Lt, g->A, g->B, g->dX);
-    GEN_TRY(loss_chunk(g, m, g->dTarg, w1, w2, nullptr, g->dLoss, g->dGx));
+    {
+      const nmc_status s = loss_chunk(g, m, g->dTarg, w1, w2, nullptr, g->dLoss, g->dGx);
+      if (s != NMC_OK) {
+        g->err += "; batch sample ids:";
+        for (int k = 0; k < m; ++k) g->err += " " + std::to_string(ids[c0 + k]);
+        return s;
+      }
+    }
     k_grad_x_to_a2<<<blocks_for(m * osz), kThreads, 0, st>>>(g->dGx, g->dPo, m, g->Lt, g->A, g->B,
                                                               g->dGa2);
     const int acc = c0 > 0;
@@ -833,8 +886,9 @@ nmc_status nmc_gen_train_step(nmc_gen* g, const long long* ids, int n, const dou
   g->steps += 1;
   const double c1b = 1.0 - std::pow(kAdamB1, (double)g->steps);
   const double c2b = 1.0 - std::pow(kAdamB2, (double)g->steps);
+  k_clip_scale<<<1, kThreads, 0, st>>>(g->dGP, g->nP, (float)g->clip, g->dScale);
   k_adam<<<blocks_for(g->nP), kThreads, 0, st>>>(g->dP, g->dGP, g->dM, g->dV, g->nP, (float)lr,
-                                                 (float)c1b, (float)c2b);
+                                                 (float)c1b, (float)c2b, g->dScale);
   GEN_CUDA(g, cudaGetLastError());
   GEN_CUDA(g, cudaStreamSynchronize(st));
   if (loss_out) *loss_out = total;
@@ -859,8 +913,9 @@ nmc_status nmc_gen_train(nmc_gen* g, const double* targets, int n, int epochs, i
   std::vector<double> tb;
   for (int e = 0; e < epochs; ++e) {
     for (int k = 0; k < n; ++k) order[k] = k;
+    const uint32_t ep = (uint32_t)g->epochs;
     for (int k = n - 1; k > 0; --k) {  // Fisher-Yates, uniforms at (k, epoch, 0, 5)
-      uint32_t c[4] = {(uint32_t)k, (uint32_t)e, 0u, kTagShuffle};
+      uint32_t c[4] = {(uint32_t)k, ep, 0u, kTagShuffle};
       philox4x32_10(c, k0, k1);
       const int r = (int)(((uint64_t)c[0] * (uint64_t)(k + 1)) >> 32);
       std::swap(order[k], order[r]);
@@ -879,11 +934,18 @@ nmc_status nmc_gen_train(nmc_gen* g, const double* targets, int n, int epochs, i
       sum += L;
     }
     if (epoch_loss) epoch_loss[e] = sum / n;
+    ++g->epochs;
   }
   return NMC_OK;
 }
 
 long long nmc_gen_steps(const nmc_gen* g) { return g ? g->steps : -1; }
+
+nmc_status nmc_gen_set_clip(nmc_gen* g, double max_norm) {
+  if (!g || !(max_norm >= 0)) return NMC_EINVAL;
+  g->clip = max_norm;
+  return NMC_OK;
+}
 
 const char* nmc_gen_last_error(const nmc_gen* g) { return g ? g->err.c_str() : "null generator"; }
 

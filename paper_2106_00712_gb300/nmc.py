@@ -73,7 +73,7 @@ EXPORTED_GEN = ("nmc_gen_paper_arch", "nmc_gen_create", "nmc_gen_get_params",
                 "nmc_gen_set_params", "nmc_gen_probs", "nmc_gen_sample_fields",
                 "nmc_gen_observables", "nmc_gen_generated_observables",
                 "nmc_gen_loss_grad", "nmc_gen_train_step",
-                "nmc_gen_train", "nmc_gen_steps", "nmc_gen_last_error", "nmc_gen_destroy")
+                "nmc_gen_train", "nmc_gen_steps", "nmc_gen_set_clip", "nmc_gen_last_error", "nmc_gen_destroy")
 
 
 class KernelStat(ctypes.Structure):
@@ -139,6 +139,7 @@ def load():
         "nmc_gen_train_step": (i, [vp, vp, i, vp, d, d, d, P(d)]),
         "nmc_gen_train": (i, [vp, vp, i, i, i, d, d, d, vp]),
         "nmc_gen_steps": (ctypes.c_longlong, [vp]),
+        "nmc_gen_set_clip": (i, [vp, d]),
         "nmc_gen_last_error": (ctypes.c_char_p, [vp]),
         "nmc_gen_destroy": (None, [vp]),
     }
@@ -558,3 +559,6 @@ class Generator:
 
     def steps(self):
         return load().nmc_gen_steps(self.g)
+
+    def set_clip(self, max_norm):
+        _gcheck(self.g, load().nmc_gen_set_clip(self.g, max_norm))

@@ -223,3 +223,20 @@ def test_series_is_consistent_with_measure(env):
     for ch in range(4):
         for k, name in enumerate(("energy", "ekin", "double_occ", "s_pipi", "density")):
             assert abs(ser[:, ch, k].mean() - getattr(per[ch], name).mean) < 1e-12
+
+
+def test_gradient_clip_bounds_the_step(env):
+    """With a tiny bound the clipped gradient is far below Adam's epsilon, so the first
+    step moves no parameter by more than lr * 1e-3; without a bound it moves by ~lr."""
+    torch, nmc = env
+    rng = np.random.default_rng(6)
+    tg = np.stack([rng.uniform(0.3, 0.6, 2), rng.uniform(-1.6, -1.2, 2)], axis=1)
+    moved = []
+    for clip in (1e-12, 0.0):
+        with _gen(nmc, TINY, arch=TINY_ARCH, seed=8, max_batch=2) as g:
+            g.set_clip(clip)
+            before = [a.copy() for pr in g.params() for a in pr]
+            g.train_step(np.array([0, 1]), tg, 2.0, 0.5, 1e-3)
+            after = [a for pr in g.params() for a in pr]
+            moved.append(max(float(np.max(np.abs(a - b))) for a, b in zip(after, before)))
+    assert moved[0] < 1e-6 and moved[1] > 5e-4, moved
