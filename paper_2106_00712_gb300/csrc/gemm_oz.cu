@@ -76,14 +76,26 @@ __device__ __forceinline__ void slice_value(df2 v, int e, __nv_bfloat16* out, in
   }
 }
 
-__device__ __forceinline__ int field_m_oz(const int8_t* f, long long fstride, int ns, int b,
-                                          int r, int c, int kr, int kc) {
-  const int sg = (ns == 2 && (b & 1)) ? -1 : 1;
-  const int8_t* fb = f + (long long)(ns == 2 ? b >> 1 : b) * fstride;
-  int m = 0;
-  if (kr) m += kr * (fb[r] > 0 ? 1 : -1);
-  if (kc) m += kc * (fb[c] > 0 ? 1 : -1);
-  return sg * m;
+// Asynchronous global -> shared copies (LDGSTS): issued back to back by every thread, so
+// the operand loads of a CTA cost one memory latency instead of one per loop iteration.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+// 8 bytes, zero-filled when src_bytes = 0 (nothing is read then)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int src_bytes) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(a), "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory"); }
+
+// sigma * lam multiple m = sigma (kr s(r) + kc s(c)) from a chain's field row held in shared
+// memory (sf[i] = s(i, l) in {-1, +1})
+__device__ __forceinline__ int field_m_sm(const int8_t* sf, int sg, int r, int c, int kr, int kc) {
+  return sg * (kr * sf[r] + kc * sf[c]);
 }
 
 // Shared memory: const slices [kS][kNP][kLd] bf16, chain slices [kS][kNP][kLd] bf16,
@@ -98,31 +110,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const DfGemmArgs g) {
   __nv_bfloat16* Xs = (__nv_bfloat16*)(smraw + kSliceBytes);  // chain operand slices
   df2* stage = (df2*)(smraw + 2 * kSliceBytes);
   int* xexp = (int*)(stage + kNP * kNP);
+  __shared__ int8_t sfb[kNP], sfc[kNP];   // field rows of this chain (B staging, epilogue)
   const int N = g.N, b = blockIdx.x, tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
+  const int sg = (g.ns == 2 && (b & 1)) ? -1 : 1;
+  const long long fchain = (long long)(g.ns == 2 ? b >> 1 : b) * g.fstride;
 
-  // constant operand slices (prepared with the matching row/column scaling)
-  {
-    const uint4* src = (const uint4*)g.oz_const;
-    uint4* dst = (uint4*)Cs;
-    for (int e = tid; e < (int)(kSliceBytes / 16); e += kThreads) dst[e] = src[e];
-  }
-  // chain operand: stage as FP32 pairs (zero padding), field scaling when it is B
+  // chain operand (group 0) and constant operand slices (group 1), both asynchronous; the
+  // constant slices (prepared with the matching row/column scaling) are needed only by the
+  // MMAs, so the staging and slicing below proceed while they arrive
   const df2* X = CONST_A ? g.B + (long long)b * g.sB : g.A + (long long)b * g.sA;
   const int ldx = CONST_A ? g.ldb : g.lda;
   for (int e = tid; e < kNP * kNP; e += kThreads) {
     const int r = e >> 6, c = e & 63;
-    df2 v = df_zero();
-    if (r < N && c < N) {
-      v = X[(long long)r * ldx + c];
-      if (CONST_A && g.bfields) {
-        const int m = field_m_oz(g.bfields, g.fstride, g.ns, b, r, c, g.br, g.bc);
-        if (m) v = df_mul(v, g.e[m + 2]);
-      }
-    }
-    stage[e] = v;
+    const bool in = r < N && c < N;
+    cp_async8(stage + e, in ? (const void*)(X + (long long)r * ldx + c) : (const void*)X, in ? 8 : 0);
   }
+  cp_async_commit();
+  {
+    const uint4* src = (const uint4*)g.oz_const;
+    for (int e = tid; e < (int)(kSliceBytes / 16); e += kThreads) cp_async16(Cs + e * 8, src + e);
+  }
+  cp_async_commit();
+  if (tid < kNP) {
+    sfb[tid] = (g.bfields && tid < N) ? (g.bfields[fchain + tid] > 0 ? 1 : -1) : 1;
+    sfc[tid] = (g.cfields && tid < N) ? (g.cfields[fchain + tid] > 0 ? 1 : -1) : 1;
+  }
+  cp_async_wait<1>();   // the chain operand has landed (this thread's copies)
   __syncthreads();
+  if (CONST_A && g.bfields) {  // field scaling of the chain operand when it is B
+    for (int e = tid; e < kNP * kNP; e += kThreads) {
+      const int r = e >> 6, c = e & 63;
+      const int m = field_m_sm(sfb, sg, r, c, g.br, g.bc);
+      if (m && r < N && c < N) stage[e] = df_mul(stage[e], g.e[m + 2]);
+    }
+    __syncthreads();
+  }
   // scale exponents: per column of B (chain = B) or per row of A (chain = A)
   if (tid < kNP) {
     float mx = 0.f;
@@ -139,6 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const DfGemmArgs g) {
     const int ex = CONST_A ? xexp[c] : xexp[r];
     slice_value(stage[e], ex, Xs + r * kLd + c, kNP * kLd);
   }
+  cp_async_wait<0>();   // the constant slices have landed (this thread's copies)
   __syncthreads();
 
   const __nv_bfloat16* As = CONST_A ? Cs : Xs;
@@ -191,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const DfGemmArgs g) {
       const int ex = CONST_A ? cexp[i] + xexp[c] : xexp[i] + cexp[c];
       df2 out{ldexpf(sum.hi, ex), ldexpf(sum.lo, ex)};
       if (g.cfields) {
-        const int m = field_m_oz(g.cfields, g.fstride, g.ns, b, i, c, g.cr, g.cc);
+        const int m = field_m_sm(sfc, sg, i, c, g.cr, g.cc);
         if (m) out = df_mul(out, g.e[m + 2]);
       }
       const long long idx = (long long)b * g.sC + (long long)i * g.ldc + c;
