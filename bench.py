@@ -54,10 +54,69 @@ PEAK_SOURCE = {
     "fp32": "152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (derived)",
     "fp32x2": "FP32 pipe (152 x 128 x 2 x 2.07 GHz) / 12 instructions per compensated FMA",
 }
-# DRAM bytes per launch of the dominant kernel, from an ncu capture of the same launch
-# configuration (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the
-# kernel source at capture time; reported as null once the source has changed.
-TRAFFIC = {}
+# DRAM bytes per launch of a kernel, from an ncu capture of the same launch configuration
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel source at
+# capture time; reported as null once the source has changed.
+TRAFFIC = {
+    # k_gemm_oz, bench launch configuration (512 products of 64 x 64), ncu --set full
+    # (cold cache): 16.94 MB read, 0 written -- the chain operand once, no re-reads
+    "gemm_oz.cu": ("2fa9572c8b6c43e7", 16.93e6),
+}
+
+
+def traffic_of(src):
+    """DRAM bytes per launch from the ncu capture, or None if the source changed since."""
+    h, b = TRAFFIC.get(src, (None, None))
+    return b if h is not None and h == src_hash(src) else None
+
+
+def class_rooflines(st, base, impl, ns, acc):
+    """Achieved vs peak for each timed kernel class of the path (algorithmic work per launch
+    / average event-timed launch duration). Per launch, every class runs over the batch of
+    ns x chains matrices of N x N: products 2N^3 each; QR with Q formed 8/3 N^3; Gauss-Jordan
+    on [X | N right-hand sides] 3N^3; a slice of flips, per accepted flip and spin, a rank-k
+    flush share 2N^2 plus the panel column and row 2Nk (k = delay)."""
+    N, C, k = WL.N, WL.n_chains, WL.delay_k
+    batch = ns * C
+    def rate(cls, flop):
+        launches, timed, ms = st[cls]
+        return flop / (ms / max(timed, 1) * 1e-3) / 1e12
+    out = {}
+    if st.get("gemm_tc", (0,))[0]:
+        a = rate("gemm_tc", OZ_PRODUCTS * 2.0 * N ** 3 * batch)
+        out["gemm_tc"] = {"bound": "tensor", "kernel": "k_gemm_oz (BF16 mma.sync, exact 7x7-slice products)",
+                          "achieved": a, "peak": BF16_PEAK, "unit": "TFLOP/s", "frac": a / BF16_PEAK,
+                          "traffic": traffic_of("gemm_oz.cu"),
+                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
+                          "algorithmic": f"{OZ_PRODUCTS} BF16 slice products of 2N^3 per product"}
+    for cls, kname, peak, src in (
+            ("gemm_df", "k_gemm_df<64,64> (compensated FP32 pairs)", PEAK_TFLOPS["fp32x2"], PEAK_SOURCE["fp32x2"]),
+            ("gemm", {"fp64": "k_gemm<double,64>", "fp32": "k_gemm<float,64>",
+                      "fp32x2": "k_gemm<double,64> (FP64 recompute, T updates)"}[base],
+             PEAK_TFLOPS["fp32" if base == "fp32" else "fp64"],
+             PEAK_SOURCE["fp32" if base == "fp32" else "fp64"])):
+        if st.get(cls, (0,))[0]:
+            a = rate(cls, 2.0 * N ** 3 * batch)
+            out[cls] = {"bound": "alu", "kernel": kname, "achieved": a, "peak": peak,
+                        "unit": "TFLOP/s", "frac": a / peak, "traffic": None, "peak_source": src}
+    if st.get("flip", (0,))[0]:
+        a = rate("flip", acc * N * C * ns * (2.0 * N * N + 2.0 * N * k))
+        fpk = PEAK_TFLOPS[base]
+        out["flip"] = {"bound": "alu", "kernel": {"fp64": "k_flip<double>", "fp32": "k_flip<float>",
+                                                  "fp32x2": "k_flip_df"}[base],
+                       "achieved": a, "peak": fpk, "unit": "TFLOP/s", "frac": a / fpk,
+                       "traffic": None, "peak_source": PEAK_SOURCE[base],
+                       "algorithmic": "per accepted flip and spin 2N^2 + 2Nk (delayed rank-k updates); "
+                                      "one launch = one slice of every chain; latency-bound (one "
+                                      "sequential site loop per chain)"}
+    for cls, kname, flop in (("qrp", "k_qrp (FP64 column-pivoted QR + Q)", 8.0 / 3.0 * N ** 3),
+                             ("solve", "k_solve (FP64 Gauss-Jordan)", 3.0 * N ** 3)):
+        if st.get(cls, (0,))[0]:
+            a = rate(cls, flop * batch)
+            out[cls] = {"bound": "alu", "kernel": kname, "achieved": a, "peak": PEAK_TFLOPS["fp64"],
+                        "unit": "TFLOP/s", "frac": a / PEAK_TFLOPS["fp64"], "traffic": None,
+                        "peak_source": PEAK_SOURCE["fp64"]}
+    return out
 
 
 def src_hash(name):
@@ -330,26 +389,11 @@ def main():
     per_launch_flop = 2.0 * WL.N ** 3 * ns * WL.n_chains  # batched N x N x N, ns per chain
     tot_ms = max(sum(x[2] for x in st.values()), 1e-30)
     share = {k: v[2] / tot_ms for k, v in st.items() if v[0]}
-    if base == "fp32x2" and impl == 0 and st.get("gemm_tc", (0,))[0]:
-        # tensor-core products: the issued work is OZ_PRODUCTS BF16 slice products each
-        g_launch, g_timed, g_ms = st["gemm_tc"]
-        achieved = OZ_PRODUCTS * per_launch_flop / (g_ms / max(g_timed, 1) * 1e-3) / 1e12
-        roofline = {"bound": "tensor", "kernel": "k_gemm_oz (BF16 mma.sync, exact 7x7-slice products)",
-                    "achieved": achieved, "peak": BF16_PEAK, "unit": "TFLOP/s",
-                    "frac": achieved / BF16_PEAK, "traffic": None,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
-                    "algorithmic": f"{OZ_PRODUCTS} BF16 slice products per FP64-class product",
-                    "dominant_class": dom, "share": share}
-    else:
-        gcls = "gemm_df" if base == "fp32x2" else "gemm"
-        g_launch, g_timed, g_ms = st[gcls]
-        achieved = per_launch_flop / (g_ms / max(g_timed, 1) * 1e-3) / 1e12
-        peak = PEAK_TFLOPS[base]
-        kname = {"fp64": "k_gemm<double,64>", "fp32": "k_gemm<float,64>",
-                 "fp32x2": "k_gemm_df<64,64> (compensated FP32 pairs)"}[base]
-        roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": PEAK_SOURCE[base], "dominant_class": dom, "share": share}
+    rl = class_rooflines(st, base, impl, ns, r["obs"].accept)
+    roofline = dict(rl.get(dom) or rl[max(rl, key=lambda k: st[k][2])])
+    roofline.update({"dominant_class": dom, "share": share})
+    roofline["others"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "frac")}
+                          for k, v in rl.items() if k != dom}
 
     e2e_dt, h2d, d2h, _ = run_e2e(nmc, torch, best, args.steps, rank, stream)
     e2e = {"value": flips_per_step * args.steps / e2e_dt * world, "unit": UNIT,

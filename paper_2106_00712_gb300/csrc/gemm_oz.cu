@@ -11,8 +11,9 @@
 // and g <= S + 1 (28 slice products) the dropped terms are ~2^-49 of the row/column maxima
 // -- the precision of the double-float SIMT path, at tensor-core throughput.
 //
-// One CTA per N x N matrix (N <= 64, zero-padded to 64), 16 warps, each warp a 16 x 16
-// output block (two m16n8k16 n-tiles) with 7 group accumulators. One operand is a shared
+// Two CTAs per N x N product (N <= 64, zero-padded to 64), each computing one 64 x 32 half
+// with 8 warps; each warp a 16 x 16 output block (two m16n8k16 n-tiles) with 7 group
+// accumulators. One operand is a shared
 // constant (e^{-+dtau K}, e^{-+dtau K/2}), sliced once per context; the other is the chain's
 // matrix (FP32 pairs), scaled by the field factors while staged, sliced in shared memory.
 #include <cuda_bf16.h>
@@ -27,7 +28,6 @@ constexpr int kS = 7;          // slices per operand
 constexpr int kG = kS;         // groups g = 2..S+1
 constexpr int kNP = 64;        // padded matrix size
 constexpr int kLd = kNP + 8;   // padded row (bf16) -> conflict-free ldmatrix
-constexpr int kThreads = 512;  // 16 warps
 
 __device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3,
                                         const void* p) {
@@ -98,83 +98,111 @@ __device__ __forceinline__ int field_m_sm(const int8_t* sf, int sg, int r, int c
   return sg * (kr * sf[r] + kc * sf[c]);
 }
 
-// Shared memory: const slices [kS][kNP][kLd] bf16, chain slices [kS][kNP][kLd] bf16,
-// chain staging [kNP][kNP] df2, chain scale exponents [kNP] int.
+// Work split: each CTA computes half of one product, the output columns n_off..n_off+31
+// when the chain operand is B (it then needs only those 32 columns of B) or the output rows
+// m_off..m_off+31 when the chain operand is A (only those rows of A), so the chain operand is
+// sliced once in total and two CTAs share an SM: while one slices, the other's MMAs run.
+// Shared memory: constant slices [kS][kNP][kLd] bf16 (the whole constant), chain slices
+// [kS][64][40] (B half) or [kS][32][kLd] (A half) bf16; the chain operand goes from global
+// memory to registers to slices (no staging buffer).
+constexpr int kHalf = kNP / 2;
+constexpr int kLdH = kHalf + 8;  // padded row of a B half -> conflict-free ldmatrix
+constexpr int kThreadsH = 256;   // 8 warps, each a 16 x 16 output block of the 64 x 32 half
 constexpr size_t kSliceBytes = (size_t)kS * kNP * kLd * sizeof(__nv_bfloat16);
-constexpr size_t kSmemBytes = 2 * kSliceBytes + (size_t)kNP * kNP * sizeof(df2) + kNP * 4 + 64;
+constexpr size_t kHalfBytesB = (size_t)kS * kNP * kLdH * sizeof(__nv_bfloat16);
+constexpr size_t kHalfBytesA = (size_t)kS * kHalf * kLd * sizeof(__nv_bfloat16);
+constexpr size_t kHalfBytes = kHalfBytesB > kHalfBytesA ? kHalfBytesB : kHalfBytesA;
+constexpr size_t kSmemBytes = kSliceBytes + kHalfBytes;
+constexpr int kPerThread = kNP * kHalf / kThreadsH;  // chain elements per thread (8)
 
 template <bool CONST_A>
-__global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const DfGemmArgs g) {
+__global__ void __launch_bounds__(kThreadsH, 2) k_gemm_oz(const DfGemmArgs g) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  __nv_bfloat16* Cs = (__nv_bfloat16*)smraw;             // constant operand slices
-  __nv_bfloat16* Xs = (__nv_bfloat16*)(smraw + kSliceBytes);  // chain operand slices
-  df2* stage = (df2*)(smraw + 2 * kSliceBytes);
-  int* xexp = (int*)(stage + kNP * kNP);
+  __nv_bfloat16* Cs = (__nv_bfloat16*)smraw;                   // constant operand slices
+  __nv_bfloat16* Xs = (__nv_bfloat16*)(smraw + kSliceBytes);   // chain operand half slices
   __shared__ int8_t sfb[kNP], sfc[kNP];   // field rows of this chain (B staging, epilogue)
-  const int N = g.N, b = blockIdx.x, tid = threadIdx.x;
+  __shared__ int smax[kHalf];             // per chain column (B) / row (A): max |hi| bits
+  __shared__ int xexp[kHalf];
+  const int N = g.N, b = blockIdx.x >> 1, half = blockIdx.x & 1, tid = threadIdx.x;
+  const int off = half * kHalf;          // n_off (chain = B) or m_off (chain = A)
+  if (off >= N) return;                  // nothing of this product in the upper half
   const int warp = tid >> 5, lane = tid & 31;
   const int sg = (g.ns == 2 && (b & 1)) ? -1 : 1;
   const long long fchain = (long long)(g.ns == 2 ? b >> 1 : b) * g.fstride;
 
-  // chain operand (group 0) and constant operand slices (group 1), both asynchronous; the
-  // constant slices (prepared with the matching row/column scaling) are needed only by the
-  // MMAs, so the staging and slicing below proceed while they arrive
-  const df2* X = CONST_A ? g.B + (long long)b * g.sB : g.A + (long long)b * g.sA;
-  const int ldx = CONST_A ? g.ldb : g.lda;
-  for (int e = tid; e < kNP * kNP; e += kThreads) {
-    const int r = e >> 6, c = e & 63;
-    const bool in = r < N && c < N;
-    cp_async8(stage + e, in ? (const void*)(X + (long long)r * ldx + c) : (const void*)X, in ? 8 : 0);
-  }
-  cp_async_commit();
+  // constant operand slices (prepared with the matching row/column scaling): asynchronous,
+  // needed only by the MMAs
   {
     const uint4* src = (const uint4*)g.oz_const;
-    for (int e = tid; e < (int)(kSliceBytes / 16); e += kThreads) cp_async16(Cs + e * 8, src + e);
+    for (int e = tid; e < (int)(kSliceBytes / 16); e += kThreadsH) cp_async16(Cs + e * 8, src + e);
   }
   cp_async_commit();
   if (tid < kNP) {
     sfb[tid] = (g.bfields && tid < N) ? (g.bfields[fchain + tid] > 0 ? 1 : -1) : 1;
     sfc[tid] = (g.cfields && tid < N) ? (g.cfields[fchain + tid] > 0 ? 1 : -1) : 1;
   }
-  cp_async_wait<1>();   // the chain operand has landed (this thread's copies)
-  __syncthreads();
-  if (CONST_A && g.bfields) {  // field scaling of the chain operand when it is B
-    for (int e = tid; e < kNP * kNP; e += kThreads) {
-      const int r = e >> 6, c = e & 63;
-      const int m = field_m_sm(sfb, sg, r, c, g.br, g.bc);
-      if (m && r < N && c < N) stage[e] = df_mul(stage[e], g.e[m + 2]);
-    }
-    __syncthreads();
+  if (tid < kHalf) smax[tid] = 0;
+  // chain operand half into registers: element j of this thread is e = tid + j * 256 of the
+  // 64 x 32 (B: rows k, columns off + c) or 32 x 64 (A: rows off + r, columns k) block
+  const df2* X = CONST_A ? g.B + (long long)b * g.sB : g.A + (long long)b * g.sA;
+  const int ldx = CONST_A ? g.ldb : g.lda;
+  df2 v[kPerThread];
+#pragma unroll
+  for (int j = 0; j < kPerThread; ++j) {
+    const int e = tid + j * kThreadsH;
+    const int r = CONST_A ? (e >> 5) : off + (e >> 6);
+    const int c = CONST_A ? off + (e & 31) : (e & 63);
+    v[j] = (r < N && c < N) ? X[(long long)r * ldx + c] : df_zero();
   }
-  // scale exponents: per column of B (chain = B) or per row of A (chain = A)
-  if (tid < kNP) {
-    float mx = 0.f;
-    for (int k = 0; k < kNP; ++k) {
-      const df2 v = CONST_A ? stage[k * kNP + tid] : stage[tid * kNP + k];
-      mx = fmaxf(mx, fabsf(v.hi));
+  __syncthreads();   // field rows and smax initialised
+#pragma unroll
+  for (int j = 0; j < kPerThread; ++j) {
+    const int e = tid + j * kThreadsH;
+    const int r = CONST_A ? (e >> 5) : off + (e >> 6);
+    const int c = CONST_A ? off + (e & 31) : (e & 63);
+    if (CONST_A && g.bfields) {
+      const int m = field_m_sm(sfb, sg, r, c, g.br, g.bc);
+      if (m && r < N && c < N) v[j] = df_mul(v[j], g.e[m + 2]);
     }
+    // non-negative floats order like their bit patterns
+    atomicMax(&smax[CONST_A ? (e & 31) : (e >> 6)], __float_as_int(fabsf(v[j].hi)));
+  }
+  __syncthreads();
+  if (tid < kHalf) {
+    const float mx = __int_as_float(smax[tid]);
     // |hi + lo| <= |hi| (1 + 2^-24): one extra bit of headroom
     xexp[tid] = scale_exp(mx) + (mx > 0.f ? 1 : 0);
   }
   __syncthreads();
-  for (int e = tid; e < kNP * kNP; e += kThreads) {
-    const int r = e >> 6, c = e & 63;
-    const int ex = CONST_A ? xexp[c] : xexp[r];
-    slice_value(stage[e], ex, Xs + r * kLd + c, kNP * kLd);
+#pragma unroll
+  for (int j = 0; j < kPerThread; ++j) {
+    const int e = tid + j * kThreadsH;
+    if (CONST_A) {
+      const int r = e >> 5, c = e & 31;
+      slice_value(v[j], xexp[c], Xs + r * kLdH + c, kNP * kLdH);
+    } else {
+      const int r = e >> 6, c = e & 63;
+      slice_value(v[j], xexp[r], Xs + r * kLd + c, kHalf * kLd);
+    }
   }
   cp_async_wait<0>();   // the constant slices have landed (this thread's copies)
   __syncthreads();
 
+  // A operand [m][k], B operand [k][n]; warp block: 16 rows x 16 columns
   const __nv_bfloat16* As = CONST_A ? Cs : Xs;
   const __nv_bfloat16* Bs = CONST_A ? Xs : Cs;
-  const int m0 = (warp >> 2) * 16, n0 = (warp & 3) * 16;
+  const int ldA = kLd, sliceA = CONST_A ? kNP * kLd : kHalf * kLd;
+  const int ldB = CONST_A ? kLdH : kLd, sliceB = CONST_A ? kNP * kLdH : kNP * kLd;
+  // local block origin: B half 64 x 32 -> 4 x 2 warps; A half 32 x 64 -> 2 x 4 warps
+  const int m0 = CONST_A ? (warp >> 1) * 16 : (warp >> 2) * 16;
+  const int n0 = CONST_A ? (warp & 1) * 16 : (warp & 3) * 16;
   float acc[kG][2][4];
 #pragma unroll
   for (int q = 0; q < kG; ++q)
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[q][j][v] = 0.f;
+      for (int w = 0; w < 4; ++w) acc[q][j][w] = 0.f;
 
 #pragma unroll 1
   for (int k0 = 0; k0 < kNP; k0 += 16) {
@@ -182,13 +210,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const DfGemmArgs g) {
 #pragma unroll
     for (int t = 0; t < kS; ++t) {
       const __nv_bfloat16* pb =
-          Bs + t * kNP * kLd + (k0 + (lane & 7) + ((lane >> 3) & 1) * 8) * kLd + n0 + (lane >> 4) * 8;
+          Bs + t * sliceB + (k0 + (lane & 7) + ((lane >> 3) & 1) * 8) * ldB + n0 + (lane >> 4) * 8;
       ldsm_x4_t(bf[t][0], bf[t][1], bf[t][2], bf[t][3], pb);
     }
 #pragma unroll
     for (int s = 0; s < kS; ++s) {
       uint32_t af[4];
-      const __nv_bfloat16* pa = As + s * kNP * kLd + (m0 + (lane & 15)) * kLd + k0 + (lane >> 4) * 8;
+      const __nv_bfloat16* pa = As + s * sliceA + (m0 + (lane & 15)) * ldA + k0 + (lane >> 4) * 8;
       ldsm_x4(af[0], af[1], af[2], af[3], pa);
 #pragma unroll
       for (int t = 0; t < kS; ++t)
@@ -204,15 +232,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_oz(const DfGemmArgs g) {
 #pragma unroll
   for (int j = 0; j < 2; ++j)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int i = m0 + (lane >> 2) + ((v >> 1) << 3);
-      const int c = n0 + j * 8 + (lane & 3) * 2 + (v & 1);
+    for (int w = 0; w < 4; ++w) {
+      const int il = m0 + (lane >> 2) + ((w >> 1) << 3);
+      const int cl = n0 + j * 8 + (lane & 3) * 2 + (w & 1);
+      const int i = CONST_A ? il : off + il;
+      const int c = CONST_A ? off + cl : cl;
       if (i >= N || c >= N) continue;
       df2 sum = df_zero();
 #pragma unroll
       for (int q = kG - 1; q >= 0; --q)
-        sum = df_add(sum, df2{ldexpf(acc[q][j][v], -8 * (q + 2)), 0.f});
-      const int ex = CONST_A ? cexp[i] + xexp[c] : xexp[i] + cexp[c];
+        sum = df_add(sum, df2{ldexpf(acc[q][j][w], -8 * (q + 2)), 0.f});
+      const int ex = CONST_A ? cexp[i] + xexp[cl] : xexp[il] + cexp[c];
       df2 out{ldexpf(sum.hi, ex), ldexpf(sum.lo, ex)};
       if (g.cfields) {
         const int m = field_m_sm(sfc, sg, i, c, g.cr, g.cc);
@@ -264,13 +294,13 @@ bool gemm_oz_supported(int N) { return N <= kNP; }
 
 void gemm_oz(const DfGemmArgs& g, bool const_is_a, cudaStream_t st) {
   if (g.batch <= 0) return;
-  if (const_is_a) {
-    allow_max_dynamic_smem((const void*)k_gemm_oz<true>);
-    k_gemm_oz<true><<<g.batch, kThreads, kSmemBytes, st>>>(g);
-  } else {
-    allow_max_dynamic_smem((const void*)k_gemm_oz<false>);
-    k_gemm_oz<false><<<g.batch, kThreads, kSmemBytes, st>>>(g);
-  }
+  const void* f = const_is_a ? (const void*)k_gemm_oz<true> : (const void*)k_gemm_oz<false>;
+  allow_max_dynamic_smem(f);
+  prefer_max_shared_carveout(f);
+  if (const_is_a)
+    k_gemm_oz<true><<<2 * g.batch, kThreadsH, kSmemBytes, st>>>(g);
+  else
+    k_gemm_oz<false><<<2 * g.batch, kThreadsH, kSmemBytes, st>>>(g);
 }
 
 }  // namespace nmc

@@ -170,6 +170,20 @@ int grid_for(long long n) {
 // stream-ordered: lowering it for one launch can break a larger launch of the same kernel
 // still queued on another stream. So each kernel's limit is raised once per device to the
 // device's opt-in maximum and never lowered.
+void prefer_max_shared_carveout(const void* func) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({func, dev})) return;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess)
+    done.insert({func, dev});
+  else
+    cudaGetLastError();
+}
+
 void allow_max_dynamic_smem(const void* func) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return;

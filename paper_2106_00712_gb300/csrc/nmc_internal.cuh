@@ -164,6 +164,9 @@ size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem, int ns);
 // ---------------------------------------------------------------------------- misc
 // Raise a kernel's dynamic shared-memory limit to the device maximum (once per device).
 void allow_max_dynamic_smem(const void* func);
+// Prefer the largest shared-memory carveout for a kernel (once per device), so that several
+// of its CTAs fit on an SM.
+void prefer_max_shared_carveout(const void* func);
 void init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0, uint32_t k1,
                  long long chain_offset, cudaStream_t st);
 void set_identity_batch(double* U, double* D, double* T, int N, int batch, cudaStream_t st);
