@@ -61,6 +61,10 @@ TRAFFIC = {
     # k_gemm_oz, bench launch configuration (512 products of 64 x 64), ncu --set full
     # (cold cache): 16.94 MB read, 0 written -- the chain operand once, no re-reads
     "gemm_oz.cu": ("2fa9572c8b6c43e7", 16.93e6),
+    # k_flip_df, same configuration (one slice of 256 chains x 2 spins), ncu --metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum (cold cache): 16.86 MB read (G as FP32
+    # pairs, once), 0 written
+    "flip.cu": ("6e32b16c0a79e4ee", 16.86e6),
 }
 
 
@@ -105,7 +109,8 @@ def class_rooflines(st, base, impl, ns, acc):
         out["flip"] = {"bound": "alu", "kernel": {"fp64": "k_flip<double>", "fp32": "k_flip<float>",
                                                   "fp32x2": "k_flip_df"}[base],
                        "achieved": a, "peak": fpk, "unit": "TFLOP/s", "frac": a / fpk,
-                       "traffic": None, "peak_source": PEAK_SOURCE[base],
+                       "traffic": traffic_of("flip.cu") if base == "fp32x2" else None,
+                       "peak_source": PEAK_SOURCE[base],
                        "algorithmic": "per accepted flip and spin 2N^2 + 2Nk (delayed rank-k updates); "
                                       "one launch = one slice of every chain; latency-bound (one "
                                       "sequential site loop per chain)"}
