@@ -252,10 +252,33 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
   }
   __syncthreads();
 
+  // Per attempt: every thread first computes its entries of column i and row i of G^ into
+  // panel slot m (they do not depend on the decision) while the last thread evaluates the
+  // ratio; after the barrier an acceptance only scales the column by the coefficient and
+  // updates the running diagonal, and a rejection leaves slot m to the next attempt. The
+  // ratio's latency thus hides behind the panel products instead of adding to them. Flags
+  // are double-buffered by attempt parity (see k_flip).
   const df2 one{1.f, 0.f};
+  const int rt = blockDim.x - 1;
   int m = 0;
   for (int i = 0; i < N; ++i) {
-    if (threadIdx.x == 0) {
+    for (int t = threadIdx.x; t < ns * N; t += blockDim.x) {
+      const int sp = t / N, r = t % N;
+      const df2* Gsp = G + sp * NN;
+      const df2* A_ = Ap + sp * KK * N;
+      const df2* B_ = Bp + sp * KK * N;
+      df2 ca = Gsp[(long long)r * N + i];   // column i of G^, row r
+      df2 rb = Gsp[(long long)i * N + r];   // row i of G^, column r
+      for (int q = 0; q < m; ++q) {
+        df_fma_acc(ca, A_[q * N + r], B_[q * N + i]);
+        df_fma_acc(rb, A_[q * N + i], B_[q * N + r]);
+      }
+      df2 v = df_neg(df_finish(ca));
+      if (r == i) v = df_add(v, one);
+      Ap[(sp * KK + m) * N + r] = v;          // times the coefficient once accepted
+      Bp[(sp * KK + m) * N + r] = df_finish(rb);
+    }
+    if (threadIdx.x == rt) {
       const int s = sl[i];
       const df2 gu = dg[i];
       const df2 du = (s > 0) ? f.dm2 : f.dp2;  // e^{-2 lam s} - 1
@@ -298,22 +321,10 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
     if (s_accept[i & 1]) {
       for (int t = threadIdx.x; t < ns * N; t += blockDim.x) {
         const int sp = t / N, r = t % N;
-        const df2* Gsp = G + sp * NN;
-        const df2* A_ = Ap + sp * KK * N;
-        const df2* B_ = Bp + sp * KK * N;
-        df2 ca = Gsp[(long long)r * N + i];   // column i of G^, row r
-        df2 rb = Gsp[(long long)i * N + r];   // row i of G^, column r
-        for (int q = 0; q < m; ++q) {
-          df_fma_acc(ca, A_[q * N + r], B_[q * N + i]);
-          df_fma_acc(rb, A_[q * N + i], B_[q * N + r]);
-        }
-        df2 v = df_neg(df_finish(ca));
-        if (r == i) v = df_add(v, one);
-        const df2 a = df_mul(s_coef[sp], v);
-        const df2 bb = df_finish(rb);
-        Ap[(sp * KK + m) * N + r] = a;
-        Bp[(sp * KK + m) * N + r] = bb;
-        dg[t] = df_add(dg[t], df_mul(a, bb));
+        const long long o = (long long)(sp * KK + m) * N + r;
+        const df2 a = df_mul(s_coef[sp], Ap[o]);
+        Ap[o] = a;
+        dg[t] = df_add(dg[t], df_mul(a, Bp[o]));
       }
       ++m;
       __syncthreads();
