@@ -19,12 +19,13 @@
 #include <cuda_bf16.h>
 
 #include "nmc_internal.cuh"
+#include "oz_slice.cuh"
 
 namespace nmc {
 
 namespace {
 
-constexpr int kS = 7;          // slices per operand
+constexpr int kS = kOzS;       // slices per operand
 constexpr int kG = kS;         // groups g = 2..S+1
 constexpr int kNP = 64;        // padded matrix size
 constexpr int kLd = kNP + 8;   // padded row (bf16) -> conflict-free ldmatrix
@@ -43,50 +44,11 @@ __device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& 
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(a));
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
-      "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// exponent e with |x| <= 2^e for the largest |x| given (0 -> 0)
-__device__ __forceinline__ int scale_exp(float m) {
-  if (!(m > 0.f)) return 0;
-  int e;
-  frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
-  return e;
-}
-
-// Cut v * 2^-e (exact power-of-two scaling of an FP32 pair) into kS integer slices.
-__device__ __forceinline__ void slice_value(df2 v, int e, __nv_bfloat16* out, int stride) {
-  float h = ldexpf(v.hi, 8 - e), l = ldexpf(v.lo, 8 - e);
-  for (int s = 0; s < kS; ++s) {
-    const float a = rintf(h);
-    out[s * stride] = __float2bfloat16_rn(a);  // integer with |a| <= 256: exact
-    // residual (h - a) + l as an exact pair, then scale by 2^8 for the next slice
-    const float d = __fsub_rn(h, a);           // exact (|h - a| <= 1/2)
-    const float t = __fadd_rn(d, l);
-    const float bb = __fsub_rn(t, d);
-    const float err = __fadd_rn(__fsub_rn(d, __fsub_rn(t, bb)), __fsub_rn(l, bb));
-    h = ldexpf(t, 8);
-    l = ldexpf(err, 8);
-  }
-}
-
 // Asynchronous global -> shared copies (LDGSTS): issued back to back by every thread, so
 // the operand loads of a CTA cost one memory latency instead of one per loop iteration.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
-}
-// 8 bytes, zero-filled when src_bytes = 0 (nothing is read then)
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int src_bytes) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(a), "l"(gmem), "r"(src_bytes)
-               : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int n>
