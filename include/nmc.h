@@ -84,6 +84,11 @@ typedef struct {
   int gemm_impl;         /* FP32X2 products with a constant operand: 0 = BF16 tensor cores with
                             exact integer slicing when N <= 64 (else SIMT), 1 = SIMT
                             double-float always                                  default 0  */
+  int sweep_graphs;      /* 1: after the first sweep of each direction, record one sweep as a
+                            CUDA graph and replay it (one launch per sweep instead of one per
+                            kernel; the same kernels with the same arguments, so the results
+                            are identical); not while profiling or replaying decisions.
+                            0: launch every kernel directly.                     default 1  */
 } nmc_options;
 
 typedef struct {

@@ -68,11 +68,12 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
   T* G = f.g_in_smem ? Gs : Gg;
   int8_t* fl = f.fields + ((long long)c * f.L + f.l) * N;
   const uint32_t gchain = (uint32_t)(f.chain_offset + c);
+  const uint32_t sweep = f.ctr ? (uint32_t)f.ctr[0] : f.sweep;
   const uint8_t* rp = f.replay ? f.replay + ((long long)c * f.L + f.l) * N : nullptr;
 
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     sl[i] = fl[i];
-    uint32_t ctr[4] = {(uint32_t)(f.l * N + i), f.sweep, gchain, kTagFlip};
+    uint32_t ctr[4] = {(uint32_t)(f.l * N + i), sweep, gchain, kTagFlip};
     philox4x32_10(ctr, f.key0, f.key1);
     u[i] = (double)ctr[0] * 2.3283064365386962890625e-10;  // 2^-32
   }
@@ -351,11 +352,12 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
   df2* G = f.g_in_smem ? Gs : Gg;
   int8_t* fl = f.fields + ((long long)c * f.L + f.l) * N;
   const uint32_t gchain = (uint32_t)(f.chain_offset + c);
+  const uint32_t sweep = f.ctr ? (uint32_t)f.ctr[0] : f.sweep;
   const uint8_t* rp = f.replay ? f.replay + ((long long)c * f.L + f.l) * N : nullptr;
 
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     sl[i] = fl[i];
-    uint32_t ctr[4] = {(uint32_t)(f.l * N + i), f.sweep, gchain, kTagFlip};
+    uint32_t ctr[4] = {(uint32_t)(f.l * N + i), sweep, gchain, kTagFlip};
     philox4x32_10(ctr, f.key0, f.key1);
     udf[i] = df_from_double((double)ctr[0] * 2.3283064365386962890625e-10);  // 2^-32
   }

@@ -88,7 +88,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 __global__ void __launch_bounds__(kMeasThreads)
 k_measure(const double* __restrict__ Gt, const double* __restrict__ K,
           const double* __restrict__ sign, int N, int Lx, int lattice, double U, int ns,
-          double* __restrict__ acc) {
+          double* __restrict__ acc, const long long* __restrict__ series_idx) {
+  if (series_idx) acc += *series_idx * (long long)gridDim.x * 8;
   __shared__ double red[kMeasThreads / 32];
   const int c = blockIdx.x;
   const long long NN = (long long)N * N;
@@ -139,7 +140,7 @@ k_measure(const double* __restrict__ Gt, const double* __restrict__ K,
 
 // cumulative[c] = max(cumulative[c], stab[c]); hist = max_c stab[c] (one CTA)
 __global__ void k_fold_drift(const unsigned long long* stab, unsigned long long* cumulative,
-                             unsigned long long* hist, int n) {
+                             unsigned long long* hist, long long cap, long long* idx, int n) {
   __shared__ unsigned long long red[256];
   unsigned long long m = 0;
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
@@ -154,7 +155,16 @@ __global__ void k_fold_drift(const unsigned long long* stab, unsigned long long*
       red[threadIdx.x] = red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0 && hist) *hist = red[0];
+  if (threadIdx.x == 0) {
+    const long long k = *idx;
+    if (hist && k < cap) hist[k] = red[0];
+    *idx = k + 1;
+  }
+}
+
+__global__ void k_advance(long long* ctr, int meas) {
+  ctr[0] += 1;
+  ctr[1] += meas;
 }
 
 int grid_for(long long n) {
@@ -236,13 +246,20 @@ void philox_batch(const uint32_t* c0, int n, uint32_t c1, uint32_t c2, uint32_t 
 }
 
 void fold_drift(const unsigned long long* stab, unsigned long long* cumulative,
-                unsigned long long* hist, int n_chains, cudaStream_t st) {
-  k_fold_drift<<<1, 256, 0, st>>>(stab, cumulative, hist, n_chains);
+                unsigned long long* hist, long long hist_cap, long long* hist_idx, int n_chains,
+                cudaStream_t st) {
+  k_fold_drift<<<1, 256, 0, st>>>(stab, cumulative, hist, hist_cap, hist_idx, n_chains);
+}
+
+void advance_counters(long long* ctr, int meas, cudaStream_t st) {
+  k_advance<<<1, 1, 0, st>>>(ctr, meas);
 }
 
 void measure(const double* Gt, const double* K, const double* sign, int N, int Lx, int lattice,
-             double U, double* acc, int n_chains, int ns, cudaStream_t st) {
-  k_measure<<<n_chains, kMeasThreads, 0, st>>>(Gt, K, sign, N, Lx, lattice, U, ns, acc);
+             double U, double* acc, int n_chains, int ns, cudaStream_t st,
+             const long long* series_idx) {
+  k_measure<<<n_chains, kMeasThreads, 0, st>>>(Gt, K, sign, N, Lx, lattice, U, ns, acc,
+                                               series_idx);
 }
 
 }  // namespace nmc

@@ -57,6 +57,16 @@ struct UDTView {
 };
 
 constexpr uint64_t kCkptMagic = 0x4e4d43434b505431ull;  // "NMCCKPT1"
+constexpr int kNumClasses = 8;
+
+// One sweep direction (and measuring or not) recorded as a CUDA graph. The recorded launches
+// name the UDV stack buffers by pointer, and a sweep permutes those buffers, so a graph is
+// replayed only from the buffer arrangement it was recorded at (`ptrs`).
+struct SweepGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> ptrs;
+  long long launches[kNumClasses] = {};
+};
 
 }  // namespace
 
@@ -101,7 +111,15 @@ struct nmc_ctx {
   double* dSeries = nullptr;              // [slot][chain][8]
   long long series_cap = 0, n_series = 0;
   uint8_t* dReplay = nullptr;
+  long long* dCtr = nullptr;   // device mirrors: [0] sweep_counter, [1] n_series, [2] n_hist
   std::vector<void*> allocs;
+
+  // sweeps replayed as CUDA graphs: [up, down][warm-up, measuring]
+  SweepGraph graphs[2][2];
+  bool use_graphs = true;
+  bool cap = false;                    // recording: launches go to cap_stream
+  cudaStream_t cap_stream = nullptr;
+  int direct_since_build = 0;          // direct sweeps since the stacks were last built
 
   // per-kernel accounting: launch counts always, CUDA-event brackets when prof is set
   bool prof = false;
@@ -112,7 +130,7 @@ struct nmc_ctx {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> event_pool;
 
-  cudaStream_t st() const { return (cudaStream_t)opt.cuda_stream; }
+  cudaStream_t st() const { return cap ? cap_stream : (cudaStream_t)opt.cuda_stream; }
   int chains() const { return opt.n_chains; }
   int ns() const { return opt.ph_symmetric ? 1 : 2; }
   int batch() const { return ns() * opt.n_chains; }
@@ -189,7 +207,17 @@ void resolve_events(nmc_ctx* x) {
 // Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the context stream):
 // creating or destroying one context does not synchronise the device, so other contexts'
 // work on other streams keeps running (the serving loop depends on this).
+void drop_graphs(nmc_ctx* x) {
+  for (auto& d : x->graphs)
+    for (auto& g : d) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+      g.ptrs.clear();
+    }
+}
+
 void free_all(nmc_ctx* x) {
+  drop_graphs(x);
   for (void* p : x->allocs) cudaFreeAsync(p, x->st());
   x->allocs.clear();
   x->dK = x->dEm = x->dEp = x->dEmh = x->dEph = x->dI = x->dOnes = nullptr;
@@ -212,6 +240,7 @@ void free_all(nmc_ctx* x) {
   x->dSeries = nullptr;
   x->series_cap = x->n_series = 0;
   x->dReplay = nullptr;
+  x->dCtr = nullptr;
   x->configured = false;
   x->have_fields = false;
 }
@@ -299,9 +328,11 @@ nmc_status alloc_all(nmc_ctx* x) {
   NMC_TRY(dalloc(x, &x->dDriftStab, x->chains()));
   x->hist_cap = 4096;
   NMC_TRY(dalloc(x, &x->dHist, x->hist_cap));
+  NMC_TRY(dalloc(x, &x->dCtr, 3));
   if (x->dry) return NMC_OK;
 
   cudaStream_t st = x->st();
+  NMC_CUDA(x, cudaMemsetAsync(x->dCtr, 0, 3 * sizeof(long long), st));
   const size_t mb = NN * sizeof(double);
   NMC_CUDA(x, cudaMemcpyAsync(x->dK, x->hK.data(), mb, cudaMemcpyHostToDevice, st));
   NMC_CUDA(x, cudaMemcpyAsync(x->dEm, x->hEm.data(), mb, cudaMemcpyHostToDevice, st));
@@ -487,17 +518,17 @@ void flip(nmc_ctx* x, int l, const uint8_t* replay) {
     };
     FlipArgs<df2> f{x->dG2, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                     (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
-                    x->dCounts, replay, nullptr, split(dm), split(dp), x->ns()};
+                    x->dCounts, replay, nullptr, split(dm), split(dp), x->ns(), x->dCtr};
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   } else if (x->fp32()) {
     FlipArgs<float> f{x->dGf, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                       (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
-                      x->dCounts, replay, nullptr, df2{0.f, 0.f}, df2{0.f, 0.f}, x->ns()};
+                      x->dCounts, replay, nullptr, df2{0.f, 0.f}, df2{0.f, 0.f}, x->ns(), x->dCtr};
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   } else {
     FlipArgs<double> f{x->dG, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                        (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
-                       x->dCounts, replay, nullptr, df2{0.f, 0.f}, df2{0.f, 0.f}, x->ns()};
+                       x->dCounts, replay, nullptr, df2{0.f, 0.f}, df2{0.f, 0.f}, x->ns(), x->dCtr};
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   }
 }
@@ -600,9 +631,9 @@ void recompute(nmc_ctx* x, const UDTView& R, const UDTView& L, bool drift) {
   if (x->dfp()) { g3.Cdf = x->dG2; g3.sCdf = NN; }
   launch(x, KC_GEMM, [&] { gemm(g3, st); });
   if (drift) {
-    unsigned long long* hist =
-        x->n_hist < x->hist_cap ? x->dHist + x->n_hist : nullptr;
-    launch(x, KC_OTHER, [&] { fold_drift(x->dDriftStab, x->dDrift, hist, x->chains(), st); });
+    launch(x, KC_OTHER, [&] {
+      fold_drift(x->dDriftStab, x->dDrift, x->dHist, x->hist_cap, x->dCtr + 2, x->chains(), st);
+    });
     ++x->n_hist;
   }
 }
@@ -610,7 +641,7 @@ void recompute(nmc_ctx* x, const UDTView& R, const UDTView& L, bool drift) {
 void measure_now(nmc_ctx* x) {
   cudaStream_t st = x->st();
   const long long NN = x->NN();
-  double* acc = x->dSeries + x->n_series * (long long)x->chains() * 8;
+  double* acc = x->dSeries;   // + (device series index) * chains * 8
   if (x->dfp()) {  // G~ = e^{dtau K/2} G e^{-dtau K/2} from the pair copy of the recomputed G
     DfGemmArgs g = df_base(x, x->dEph2, 0, x->dG2, NN);
     g.C = x->dT12;
@@ -618,12 +649,12 @@ void measure_now(nmc_ctx* x) {
     DfGemmArgs h = df_base(x, x->dT12, NN, x->dEmh2, 0);
     h.Cd = x->dM1;
     df_gemm(x, h, OZ_EMH, false);
-    launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->N, x->Lx, x->lattice, x->U, acc, x->chains(), x->ns(), st); });
+    launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->N, x->Lx, x->lattice, x->U, acc, x->chains(), x->ns(), st, x->dCtr + 1); });
     return;
   }
   launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dEph, 0, x->dG, NN, x->dT1), st); });   // e^{dtau K/2} G
   launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dT1, NN, x->dEmh, 0, x->dM1), st); });  // ... e^{-dtau K/2}
-  launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->N, x->Lx, x->lattice, x->U, acc, x->chains(), x->ns(), st); });
+  launch(x, KC_MEASURE, [&] { nmc::measure(x->dM1, x->dK, x->dSign, x->N, x->Lx, x->lattice, x->U, acc, x->chains(), x->ns(), st, x->dCtr + 1); });
 }
 
 void sweep_up(nmc_ctx* x, bool meas, const uint8_t* replay) {
@@ -678,6 +709,14 @@ void build_stacks(nmc_ctx* x, bool for_up) {
   }
 }
 
+// Copy the host counters to their device mirrors (the kernels read the device copies).
+nmc_status push_counters(nmc_ctx* x) {
+  const long long h[3] = {x->sweep_counter, x->n_series, x->n_hist};
+  NMC_CUDA(x, cudaMemcpyAsync(x->dCtr, h, sizeof h, cudaMemcpyHostToDevice, x->st()));
+  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  return NMC_OK;
+}
+
 nmc_status reset_chain_state(nmc_ctx* x) {
   cudaStream_t st = x->st();
   std::vector<double> ones(x->chains(), 1.0);
@@ -688,6 +727,7 @@ nmc_status reset_chain_state(nmc_ctx* x) {
   NMC_CUDA(x, cudaMemsetAsync(x->dHist, 0, sizeof(unsigned long long) * x->hist_cap, st));
   x->n_hist = 0;
   x->n_series = 0;
+  NMC_TRY(push_counters(x));
   x->phase = 0;
   NMC_CUDA(x, cudaStreamSynchronize(st));
   return NMC_OK;
@@ -696,6 +736,7 @@ nmc_status reset_chain_state(nmc_ctx* x) {
 nmc_status after_fields(nmc_ctx* x) {
   NMC_TRY(reset_chain_state(x));
   build_stacks(x, true);
+  x->direct_since_build = 0;
   NMC_CUDA(x, cudaGetLastError());
   NMC_CUDA(x, cudaStreamSynchronize(x->st()));
   x->have_fields = true;
@@ -725,6 +766,7 @@ nmc_status ensure_series(nmc_ctx* x, long long need) {
   x->dSeries = p;
   x->allocs.push_back(p);
   x->series_cap = cap;
+  drop_graphs(x);   // recorded measurements address the old buffer
   return NMC_OK;
 }
 
@@ -747,11 +789,104 @@ nmc_status check_drift(nmc_ctx* x) {
   return NMC_OK;
 }
 
+std::vector<const void*> slot_state(const nmc_ctx* x) {
+  std::vector<const void*> v{x->spare.U, x->spare.D, x->spare.T};
+  for (const auto& b : x->slot) {
+    v.push_back(b.U);
+    v.push_back(b.D);
+    v.push_back(b.T);
+  }
+  return v;
+}
+
+// The stack-buffer permutation of one sweep (the swaps of sweep_up / sweep_down).
+void advance_slots(nmc_ctx* x, bool up) {
+  if (up)
+    for (int j = 0; j + 1 < x->nb; ++j) std::swap(x->spare, x->slot[j + 1]);
+  else
+    for (int j = x->nb - 1; j >= 1; --j) std::swap(x->spare, x->slot[j]);
+}
+
+// One sweep as a CUDA graph: recorded on first use (on a private stream; nothing runs while
+// recording), then replayed on the context stream. Every per-sweep value the kernels need
+// (Philox sweep counter, measurement slot, drift-history slot) is read from device
+// counters, so one recording serves every later sweep of that direction from the same
+// stack-buffer arrangement. Returns false (the caller then launches the sweep directly) when
+// graphs are off, while profiling, or if recording fails.
+bool sweep_graph(nmc_ctx* x, bool up, bool meas) {
+  if (!x->opt.sweep_graphs || !x->use_graphs || x->prof || x->direct_since_build < 2)
+    return false;
+  SweepGraph& gr = x->graphs[up ? 0 : 1][meas ? 1 : 0];
+  const std::vector<const void*> state = slot_state(x);
+  if (gr.exec && gr.ptrs != state) {
+    cudaGraphExecDestroy(gr.exec);
+    gr.exec = nullptr;
+  }
+  if (!gr.exec) {
+    if (!x->cap_stream &&
+        cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      x->use_graphs = false;
+      return false;
+    }
+    long long before[kNumClasses];
+    std::memcpy(before, x->launches, sizeof before);
+    const UDTBuf spare0 = x->spare;
+    const std::vector<UDTBuf> slot0 = x->slot;
+    const long long hist0 = x->n_hist;
+    if (cudaStreamBeginCapture(x->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      x->use_graphs = false;
+      return false;
+    }
+    x->cap = true;
+    if (up) sweep_up(x, meas, nullptr);
+    else sweep_down(x, meas, nullptr);
+    launch(x, KC_OTHER, [&] { advance_counters(x->dCtr, meas ? 1 : 0, x->st()); });
+    x->cap = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(x->cap_stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    // recording ran the host side of the sweep only: put its host state back
+    x->spare = spare0;
+    x->slot = slot0;
+    x->n_hist = hist0;
+    for (int k = 0; k < kNumClasses; ++k) {
+      gr.launches[k] = x->launches[k] - before[k];
+      x->launches[k] = before[k];
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      x->use_graphs = false;
+      return false;
+    }
+    gr.exec = exec;
+    gr.ptrs = state;
+  }
+  if (cudaGraphLaunch(gr.exec, x->st()) != cudaSuccess) {
+    cudaGetLastError();
+    x->use_graphs = false;
+    return false;
+  }
+  advance_slots(x, up);
+  x->n_hist += x->nb;   // one drift record per block
+  for (int k = 0; k < kNumClasses; ++k) x->launches[k] += gr.launches[k];
+  return true;
+}
+
 nmc_status run_sweeps(nmc_ctx* x, int n, int meas, const uint8_t* replay, bool wait = true) {
   if (meas) NMC_TRY(ensure_series(x, x->n_series + n));
   for (int s = 0; s < n; ++s) {
-    if (x->phase % 2 == 0) sweep_up(x, meas != 0, replay);
-    else sweep_down(x, meas != 0, replay);
+    const bool up = x->phase % 2 == 0;
+    if (replay || !sweep_graph(x, up, meas != 0)) {
+      if (up) sweep_up(x, meas != 0, replay);
+      else sweep_down(x, meas != 0, replay);
+      launch(x, KC_OTHER, [&] { advance_counters(x->dCtr, meas ? 1 : 0, x->st()); });
+      ++x->direct_since_build;
+    }
     NMC_CUDA(x, cudaGetLastError());
     ++x->phase;
     ++x->sweep_counter;
@@ -805,6 +940,7 @@ void nmc_default_options(nmc_options* o) {
   o->cuda_stream = nullptr;
   o->ph_symmetric = 0;
   o->gemm_impl = 0;
+  o->sweep_graphs = 1;
 }
 
 // Sites of a lattice, or 0 if the lattice and sizes are not accepted: square needs even
@@ -859,7 +995,7 @@ nmc_status nmc_configure(nmc_ctx* x, const nmc_options* o) {
   if (o) n = *o;
   if (n.n_chains < 1 || n.delay_k < 1 || (n.precision != NMC_FP64 && n.precision != NMC_FP32 && n.precision != NMC_FP32X2) ||
       n.chain_offset < 0 || n.n_chains > (1 << 20) || (n.ph_symmetric != 0 && n.ph_symmetric != 1) ||
-      (n.gemm_impl != 0 && n.gemm_impl != 1))
+      (n.gemm_impl != 0 && n.gemm_impl != 1) || (n.sweep_graphs != 0 && n.sweep_graphs != 1))
     return fail(x, NMC_EINVAL, "invalid nmc_options");
   x->opt = n;
   clamp_delay(x);
@@ -1200,7 +1336,9 @@ nmc_status nmc_restore(nmc_ctx* x, const void* buf, size_t n) {
   x->n_series = ns;
   x->sweep_counter = h[5];
   x->phase = h[6];
+  NMC_TRY(push_counters(x));
   build_stacks(x, x->phase % 2 == 0);
+  x->direct_since_build = 0;
   NMC_CUDA(x, cudaGetLastError());
   NMC_CUDA(x, cudaStreamSynchronize(st));
   x->have_fields = true;
@@ -1291,6 +1429,7 @@ void nmc_destroy(nmc_ctx* x) {
   for (cudaEvent_t e : x->event_pool) cudaEventDestroy(e);
   x->event_pool.clear();
   free_all(x);
+  if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
   delete x;
 }
 

@@ -157,6 +157,7 @@ struct FlipArgs {
   T* panels_g;               // unused (panels live in shared memory)
   df2 dm2, dp2;              // dm, dp as FP32 pairs (compensated mode)
   int ns;                    // 2 spins, or 1: spin up only, G_dn = I - P G_up^T P
+  const long long* ctr;      // device counters (ctr[0] = sweep counter) or null: use sweep
 };
 template <typename T> void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st);
 size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem, int ns);
@@ -176,16 +177,22 @@ void fields_normalize(int8_t* s, long long n, cudaStream_t st);
 void philox_batch(const uint32_t* c0, int n, uint32_t c1, uint32_t c2, uint32_t c3,
                   uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st);
 
-// Per-stabilization drift (bits of non-negative doubles): fold into the per-chain maximum
-// and write the maximum over chains to *hist (if not null).
+// Per-stabilization drift (bits of non-negative doubles): fold into the per-chain maximum,
+// write the maximum over chains to hist[*hist_idx] while *hist_idx < hist_cap, then advance
+// *hist_idx (a device counter, so the launch does not depend on host state).
 void fold_drift(const unsigned long long* stab, unsigned long long* cumulative,
-                unsigned long long* hist, int n_chains, cudaStream_t st);
+                unsigned long long* hist, long long hist_cap, long long* hist_idx, int n_chains,
+                cudaStream_t st);
+// End of a sweep: ctr[0] (sweep counter) += 1, ctr[1] (measured sweeps) += meas.
+void advance_counters(long long* ctr, int meas, cudaStream_t st);
 
 // Measurement on Gt = e^{dtau K/2} G e^{-dtau K/2}: adds per-chain sums of
 // (energy, ekin, double_occ, s_pipi, density) * sign and sign into acc[chain][8].
 constexpr int kNumObs = 6;   // energy, ekin, docc, s_pipi, density, sign
 // ns = 1: only G~up is given and G~dn = I - P G~up^T P (particle-hole symmetry).
+// series_idx (device, may be null): accumulate into acc + (*series_idx) * n_chains * 8.
 void measure(const double* Gt, const double* K, const double* sign, int N, int Lx, int lattice,
-             double U, double* acc, int n_chains, int ns, cudaStream_t st);
+             double U, double* acc, int n_chains, int ns, cudaStream_t st,
+             const long long* series_idx = nullptr);
 
 }  // namespace nmc

@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
     _fields_ = [("n_chains", ctypes.c_int), ("delay_k", ctypes.c_int),
                 ("precision", ctypes.c_int), ("drift_tol", ctypes.c_double),
                 ("chain_offset", ctypes.c_longlong), ("cuda_stream", ctypes.c_void_p),
-                ("ph_symmetric", ctypes.c_int), ("gemm_impl", ctypes.c_int)]
+                ("ph_symmetric", ctypes.c_int), ("gemm_impl", ctypes.c_int),
+                ("sweep_graphs", ctypes.c_int)]
 
 
 class Est(ctypes.Structure):
@@ -359,7 +360,7 @@ class Context:
 
     def __init__(self, Lx, Ly, t, U, beta, dtau, n_wrap, seed=0, n_chains=1, delay_k=16,
                  precision=NMC_FP64, drift_tol=0.0, chain_offset=0, stream=None,
-                 ph_symmetric=0, gemm_impl=0, lattice=NMC_SQUARE):
+                 ph_symmetric=0, gemm_impl=0, lattice=NMC_SQUARE, sweep_graphs=1):
         self.ctx = nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed, lattice)
         o = nmc_default_options()
         o.n_chains, o.delay_k, o.precision = n_chains, delay_k, precision
@@ -367,6 +368,7 @@ class Context:
         o.cuda_stream = stream
         o.ph_symmetric = int(ph_symmetric)
         o.gemm_impl = int(gemm_impl)
+        o.sweep_graphs = int(sweep_graphs)
         try:
             nmc_configure(self.ctx, o)
         except Exception:

@@ -350,3 +350,31 @@ def test_state_errors_on_device(nmc):
             nmc.nmc_configure(c.ctx, nmc.nmc_default_options())
         with pytest.raises(nmc.NmcError):
             c.green(2, 0)
+
+
+@pytest.mark.parametrize("prec,ph", [(0, 0), (2, 0), (2, 1)])
+def test_sweep_graphs_equal_direct_launches(nmc, prec, ph):
+    """Sweeps replayed from recorded CUDA graphs give the same fields, G, observables and
+    drift history as direct launches, across warm-up and measuring sweeps, a checkpoint and a
+    restore (which re-arranges the stack buffers)."""
+    model = Model(6, 4, 1.0, 4.0, 2.0, 0.1, 5, seed=21)
+    out = []
+    for graphs in (1, 0):
+        with _ctx(nmc, model, n_chains=3, precision=prec, ph_symmetric=ph, drift_tol=1e-3,
+                  sweep_graphs=graphs) as c:
+            c.generate()
+            c.sweep(5, measure=0)
+            c.sweep(4, measure=1)
+            blob = c.checkpoint()
+            c.sweep(3, measure=1)
+            c.restore(blob)
+            c.sweep(5, measure=1)
+            o = c.measure()
+            out.append((c.fields(), c.green(1, 0), o.energy.mean, o.s_pipi.mean,
+                        c.drift_history(), c.series()))
+    a, b = out
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert a[2] == b[2] and a[3] == b[3]
+    np.testing.assert_array_equal(a[4], b[4])
+    np.testing.assert_array_equal(a[5], b[5])
