@@ -1,14 +1,26 @@
-"""Network-initialized Monte Carlo end to end on the paper's Hubbard point (Algorithm 1;
-Table 2: honeycomb L = 6, 72 sites, U/t = 3.83, beta = 6, dtau = 0.1).
+"""Network-initialized Monte Carlo end to end (Algorithm 1).
 
 1. Training samples: n_train chains from random fields run n_short sweeps (unthermalized);
-   per configuration S(Gamma) and E_k at slice 0 (nmc_gen_observables).
-2. Train the generator of SM Sec. II on those observables with the Eq. 4 loss (Adam,
-   lr 1e-3, batch 3, 15 epochs as in SM Sec. II; weights = inverse target variances).
+   per configuration the observables at slice 0 (nmc_gen_observables): S (S(Gamma) on the
+   honeycomb, S(pi,pi) on the square lattice) and E_k.
+2. Train the generator (SM Sec. II structure) on those observables with the Eq. 4 loss
+   (Adam, lr 1e-3, batch 3, 15 epochs as in SM Sec. II; weights = inverse target variances).
 3. Generate n_gen configurations (input stream 1): "NN" values measured directly on
    x = 2p - 1, and Bernoulli +-1 fields for the chains.
 4. DQMC chains from the generated fields (NIMC), from random fields and from the training
-   configurations: per-sweep E_k and S(Gamma) over chains (nmc_series).
+   configurations: per-sweep means over chains of E, E_k, D and S (nmc_series), and the
+   first sweep from which each stays at equilibrium.
+
+Workloads: "honeycomb" -- the paper's Hubbard point (Table 2: L = 6, 72 sites, U/t = 3.83,
+beta = 6, dtau = 0.1) with the paper's network (10x2x2 -> 20 x 16x6x3 -> 36x6x3); "square8" --
+the 8x8 square lattice at U = 4, beta = 4 (L_tau = 40) with a network of the same structure
+sized to 40x8x8 (10x2x2 -> 20 x 11x4x4 -> 21x4x4), judged by energy and double occupancy.
+The equilibrium reference is the paper's printed values for the honeycomb (our long run) and
+a long run of random starts (200 + 200 sweeps) for the square lattice.
+
+Convergence criterion (the paper gives none in numbers): the first sweep s whose mean over
+chains is within 1 combined standard error of the reference while every later sweep stays
+within 3.
 
 The chains run in FP64 (particle-hole single spin) with n_wrap = 5: generated
 configurations can be more ordered than random or Markov-chain ones, and at n_wrap = 10
@@ -17,8 +29,8 @@ bounds each step's gradient norm (clip = 1): single-configuration estimators are
 unbounded, and without a bound one configuration's gradient (norm > 1e19) overflowed
 Adam's second moment and froze the generator.
 
-Usage: python -m paper_2106_00712_gb300.nimc_run [--train 1000] [--short 10] [--epochs 15]
-       [--batch 3] [--gen 1000] [--sweeps 60]
+Usage: python -m paper_2106_00712_gb300.nimc_run [--workload honeycomb|square8]
+       [--train 1000] [--short 10] [--epochs 15] [--batch 3] [--gen N] [--sweeps 60]
 Prints one JSON object.
 """
 import argparse
@@ -29,10 +41,18 @@ import time
 import numpy as np
 
 from . import nmc
-from .workloads import HONEYCOMB_6x6
+from .workloads import HONEYCOMB_6x6, SQUARE_8x8
 
-# long-run reference of the same library (1024 chains, 200 + 200 sweeps, FP32X2 ph)
-REFERENCE = {"ekin": (-1.35713, 0.00013), "s_gamma": (0.71756, 0.00299)}
+KEYS = ("energy", "ekin", "double_occ", "s_pipi")   # nmc_series columns 0..3
+
+WORKLOADS = {
+    "honeycomb": dict(wl=HONEYCOMB_6x6.with_(n_wrap=5), arch=None, n_gen=1000,
+                      # library long run (1024 chains, 200 + 200 sweeps, FP32X2 ph)
+                      reference={"ekin": (-1.35713, 0.00013), "s_pipi": (0.71756, 0.00299)},
+                      judge=("ekin", "s_pipi")),
+    "square8": dict(wl=SQUARE_8x8.with_(n_wrap=5), arch=dict(k1=(11, 4, 4), k2=(21, 4, 4)),
+                    n_gen=4096, reference=None, judge=("energy", "double_occ")),
+}
 
 
 def _log(out, *keys):
@@ -53,42 +73,55 @@ def _ctx(wl, chains, seed, precision, ph):
 def _curve(ctx, sweeps):
     ctx.sweep(sweeps, measure=1)
     ser = ctx.series()                      # [sweeps][chains][5]
-    return {"ekin": [_stat(ser[k, :, 1]) for k in range(ser.shape[0])],
-            "s_gamma": [_stat(ser[k, :, 3]) for k in range(ser.shape[0])]}
+    return {k: [_stat(ser[s, :, i]) for s in range(ser.shape[0])] for i, k in enumerate(KEYS)}
 
 
-def _converged_at(curve, key, ref, nsig=2.0):
-    """First sweep from which every later per-sweep mean is within nsig combined errors."""
+def _converged_at(curve, key, ref):
     m = np.array([c[0] for c in curve[key]])
     e = np.array([c[1] for c in curve[key]])
-    ok = np.abs(m - ref[0]) <= nsig * np.sqrt(e * e + ref[1] ** 2)
-    for k in range(len(ok)):
-        if ok[k:].all():
+    z = np.abs(m - ref[0]) / np.sqrt(e * e + ref[1] ** 2)
+    for k in range(len(z)):
+        if z[k] <= 1.0 and np.all(z[k:] <= 3.0):
             return k + 1
     return None
 
 
-def run(n_train=1000, n_short=10, epochs=15, batch=3, lr=1e-3, n_gen=1000, sweeps=60,
-        precision=nmc.NMC_FP64, ph=1, wl=HONEYCOMB_6x6.with_(n_wrap=5), seed=2106, clip=1.0):
+def _reference(wl, seed, precision, ph, chains=1024, warm=200, meas=200):
+    with _ctx(wl, chains, seed, precision, ph) as c:
+        c.generate()
+        c.sweep(warm, measure=0)
+        c.sweep(meas, measure=1)
+        o = c.measure()
+    return {k: (getattr(o, k).mean, getattr(o, k).err) for k in KEYS}
+
+
+def run(workload="honeycomb", n_train=1000, n_short=10, epochs=15, batch=3, lr=1e-3,
+        n_gen=None, sweeps=60, precision=nmc.NMC_FP64, ph=1, seed=2106, clip=1.0):
     import torch
-    out = {"workload": "hubbard-honeycomb-L6-U3.83-beta6", "n_train": n_train,
-           "n_short": n_short, "epochs": epochs, "batch": batch, "lr": lr, "n_gen": n_gen,
-           "sweeps": sweeps, "n_wrap": wl.n_wrap, "clip": clip}
+    spec = WORKLOADS[workload]
+    wl = spec["wl"]
+    n_gen = n_gen or spec["n_gen"]
+    out = {"workload": workload, "lattice": f"{wl.lattice} {wl.Lx}x{wl.Ly}", "U": wl.U,
+           "beta": wl.beta, "dtau": wl.dtau, "n_train": n_train, "n_short": n_short,
+           "epochs": epochs, "batch": batch, "lr": lr, "n_gen": n_gen, "sweeps": sweeps,
+           "n_wrap": wl.n_wrap, "clip": clip}
     t0 = time.perf_counter()
     # 1. training samples
     with _ctx(wl, n_train, seed + 1, precision, ph) as c:
         c.generate()
         c.sweep(n_short, measure=0)
         train_fields = c.fields()
-    gen = nmc.Generator(wl.Lx, wl.Ly, wl.t, wl.U, wl.beta, wl.dtau, wl.n_wrap, seed=seed,
-                        max_batch=64, lattice=wl.lattice)
+    arch = nmc.gen_arch(**spec["arch"]) if spec["arch"] else nmc.gen_arch()
+    out["arch"] = {"z": list(arch.z), "c1": arch.c1, "k1": list(arch.k1), "k2": list(arch.k2)}
+    gen = nmc.Generator(wl.Lx, wl.Ly, wl.t, wl.U, wl.beta, wl.dtau, wl.n_wrap, arch=arch,
+                        seed=seed, max_batch=64, lattice=wl.lattice)
     gen.set_clip(clip)
     d_x = torch.from_numpy(train_fields.astype(np.float64)).cuda()
     d_o = torch.empty((n_train, 2), dtype=torch.float64, device="cuda")
     gen.observables(d_x.data_ptr(), n_train, d_o.data_ptr())
     targets = d_o.cpu().numpy()
     del d_x
-    out["train"] = {"s_gamma": _stat(targets[:, 0]), "ekin": _stat(targets[:, 1])}
+    out["train"] = {"s_pipi": _stat(targets[:, 0]), "ekin": _stat(targets[:, 1])}
     out["t_samples_s"] = time.perf_counter() - t0
     _log(out, "train")
     # 2. training
@@ -96,7 +129,7 @@ def run(n_train=1000, n_short=10, epochs=15, batch=3, lr=1e-3, n_gen=1000, sweep
     d_o0 = torch.empty((n_gen, 2), dtype=torch.float64, device="cuda")
     gen.generated_observables(0, n_gen, 1, d_o0.data_ptr())
     nn0 = d_o0.cpu().numpy()
-    out["nn_untrained"] = {"s_gamma": _stat(nn0[:, 0]), "ekin": _stat(nn0[:, 1])}
+    out["nn_untrained"] = {"s_pipi": _stat(nn0[:, 0]), "ekin": _stat(nn0[:, 1])}
     hist = gen.train(targets, epochs=epochs, batch=batch, lr=lr)
     out["epoch_loss"] = [float(v) for v in hist]
     out["t_train_s"] = time.perf_counter() - t1
@@ -105,10 +138,13 @@ def run(n_train=1000, n_short=10, epochs=15, batch=3, lr=1e-3, n_gen=1000, sweep
     # 3. generated configurations measured directly
     gen.generated_observables(0, n_gen, 1, d_o0.data_ptr())
     nn = d_o0.cpu().numpy()
-    out["nn"] = {"s_gamma": _stat(nn[:, 0]), "ekin": _stat(nn[:, 1])}
+    out["nn"] = {"s_pipi": _stat(nn[:, 0]), "ekin": _stat(nn[:, 1])}
     _log(out, "nn")
-    # 4. chains from generated, random and training configurations
+    # reference
     t2 = time.perf_counter()
+    ref = spec["reference"] or _reference(wl, seed + 5, precision, ph)
+    out["reference"] = ref
+    # 4. chains from generated, random and training configurations
     curves = {}
     with _ctx(wl, n_gen, seed + 2, precision, ph) as c:
         c.generate(mode=1, model=gen)
@@ -121,9 +157,8 @@ def run(n_train=1000, n_short=10, epochs=15, batch=3, lr=1e-3, n_gen=1000, sweep
         curves["train"] = _curve(c, sweeps)
     gen.close()
     out["t_chains_s"] = time.perf_counter() - t2
-    out["reference"] = REFERENCE
     out["converged_at_sweep"] = {
-        k: {key: _converged_at(v, key, REFERENCE[key]) for key in ("ekin", "s_gamma")}
+        k: {key: _converged_at(v, key, ref[key]) for key in spec["judge"] if key in ref}
         for k, v in curves.items()}
     out["curves"] = curves
     return out
@@ -131,16 +166,17 @@ def run(n_train=1000, n_short=10, epochs=15, batch=3, lr=1e-3, n_gen=1000, sweep
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="honeycomb", choices=sorted(WORKLOADS))
     ap.add_argument("--train", type=int, default=1000)
     ap.add_argument("--short", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=15)
     ap.add_argument("--batch", type=int, default=3)
-    ap.add_argument("--gen", type=int, default=1000)
+    ap.add_argument("--gen", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=60)
     ap.add_argument("--clip", type=float, default=1.0)
     a = ap.parse_args()
-    print(json.dumps(run(a.train, a.short, a.epochs, a.batch, n_gen=a.gen, sweeps=a.sweeps,
-                         clip=a.clip)))
+    print(json.dumps(run(a.workload, a.train, a.short, a.epochs, a.batch, n_gen=a.gen,
+                         sweeps=a.sweeps, clip=a.clip)))
 
 
 if __name__ == "__main__":
