@@ -58,13 +58,13 @@ PEAK_SOURCE = {
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel source at
 # capture time; reported as null once the source has changed.
 TRAFFIC = {
-    # k_gemm_oz, bench launch configuration (512 products of 64 x 64), ncu --set full
-    # (cold cache): 16.94 MB read, 0 written -- the chain operand once, no re-reads
-    "gemm_oz.cu": ("2fa9572c8b6c43e7", 16.93e6),
-    # k_flip_df, same configuration (one slice of 256 chains x 2 spins), ncu --metrics
-    # dram__bytes_read.sum,dram__bytes_write.sum (cold cache): 16.86 MB read (G as FP32
-    # pairs, once), 0 written
-    "flip.cu": ("6e32b16c0a79e4ee", 16.86e6),
+    # k_gemm_oz, bench launch configuration (512 products of 64 x 64), ncu --metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum (cold cache): 16.91-16.94 MB read, 0 written
+    # -- the chain operand once, no re-reads
+    "gemm_oz.cu": ("3e554b144e5c13f0", 16.93e6),
+    # k_flip_df, same configuration (one slice of 256 chains x 2 spins): 16.90-16.92 MB read
+    # (G as FP32 pairs, once), 0 written
+    "flip.cu": ("78bf4e528e97d7eb", 16.91e6),
 }
 
 
