@@ -14,7 +14,7 @@
 Workloads: "honeycomb" -- the paper's Hubbard point (Table 2: L = 6, 72 sites, U/t = 3.83,
 beta = 6, dtau = 0.1) with the paper's network (10x2x2 -> 20 x 16x6x3 -> 36x6x3); "square8" --
 the 8x8 square lattice at U = 4, beta = 4 (L_tau = 40) with a network of the same structure
-sized to 40x8x8 (10x2x2 -> 20 x 11x4x4 -> 21x4x4), judged by energy and double occupancy.
+sized to 40x8x8 (10x2x2 -> 20 x 11x4x4 -> 21x4x4); convergence of energy and double occupancy.
 The equilibrium reference is the paper's printed values for the honeycomb (our long run) and
 a long run of random starts (200 + 200 sweeps) for the square lattice.
 
@@ -49,9 +49,9 @@ WORKLOADS = {
     "honeycomb": dict(wl=HONEYCOMB_6x6.with_(n_wrap=5), arch=None, n_gen=1000,
                       # library long run (1024 chains, 200 + 200 sweeps, FP32X2 ph)
                       reference={"ekin": (-1.35713, 0.00013), "s_pipi": (0.71756, 0.00299)},
-                      judge=("ekin", "s_pipi")),
+                      converge_on=("ekin", "s_pipi")),
     "square8": dict(wl=SQUARE_8x8.with_(n_wrap=5), arch=dict(k1=(11, 4, 4), k2=(21, 4, 4)),
-                    n_gen=4096, reference=None, judge=("energy", "double_occ")),
+                    n_gen=4096, reference=None, converge_on=("energy", "double_occ")),
 }
 
 
@@ -158,7 +158,7 @@ def run(workload="honeycomb", n_train=1000, n_short=10, epochs=15, batch=3, lr=1
     gen.close()
     out["t_chains_s"] = time.perf_counter() - t2
     out["converged_at_sweep"] = {
-        k: {key: _converged_at(v, key, ref[key]) for key in spec["judge"] if key in ref}
+        k: {key: _converged_at(v, key, ref[key]) for key in spec["converge_on"] if key in ref}
         for k, v in curves.items()}
     out["curves"] = curves
     return out
