@@ -281,10 +281,11 @@ __device__ __forceinline__ void flush_store(df2* Gsp, const float (&acc)[kOzS][4
     df2 sum = df_zero();
 #pragma unroll
     for (int q = kOzS - 1; q >= 0; --q)
-      sum = df_add(sum, df2{ldexpf(acc[q][w], -8 * (q + 2)), 0.f});
+      sum = df_add(sum, df2{acc[q][w] * pow2f(-8 * (q + 2)), 0.f});
     const int ex = er[r] + fc[cc];
     df2* gp = Gsp + (long long)r * N + cc;
-    *gp = df_add(*gp, df2{ldexpf(sum.hi, ex), ldexpf(sum.lo, ex)});
+    const float se = pow2f(ex);
+    *gp = df_add(*gp, df2{sum.hi * se, sum.lo * se});
   }
 }
 

@@ -203,9 +203,10 @@ __global__ void __launch_bounds__(kThreadsH, 2) k_gemm_oz(const DfGemmArgs g) {
       df2 sum = df_zero();
 #pragma unroll
       for (int q = kG - 1; q >= 0; --q)
-        sum = df_add(sum, df2{ldexpf(acc[q][j][w], -8 * (q + 2)), 0.f});
+        sum = df_add(sum, df2{acc[q][j][w] * pow2f(-8 * (q + 2)), 0.f});
       const int ex = CONST_A ? cexp[i] + xexp[cl] : xexp[il] + cexp[c];
-      df2 out{ldexpf(sum.hi, ex), ldexpf(sum.lo, ex)};
+      const float se = pow2f(ex);
+      df2 out{sum.hi * se, sum.lo * se};
       if (g.cfields) {
         const int m = field_m_sm(sfc, sg, i, c, g.cr, g.cc);
         if (m) out = df_mul(out, g.e[m + 2]);

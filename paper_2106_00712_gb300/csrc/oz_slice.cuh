@@ -14,6 +14,11 @@ namespace nmc {
 
 constexpr int kOzS = 7;   // slices per operand
 
+// 2^k from its bit pattern (exact); outside the normal exponent range, ldexpf.
+__device__ __forceinline__ float pow2f(int k) {
+  return (k >= -126 && k <= 127) ? __int_as_float((k + 127) << 23) : ldexpf(1.f, k);
+}
+
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                          uint32_t b1) {
   asm volatile(
@@ -33,7 +38,8 @@ __device__ __forceinline__ int scale_exp(float m) {
 
 // Cut v * 2^-e (exact power-of-two scaling of an FP32 pair) into kOzS integer slices.
 __device__ __forceinline__ void slice_value(df2 v, int e, __nv_bfloat16* out, int stride) {
-  float h = ldexpf(v.hi, 8 - e), l = ldexpf(v.lo, 8 - e);
+  const float sc = pow2f(8 - e);   // scaling by a power of two: exact
+  float h = v.hi * sc, l = v.lo * sc;
   for (int s = 0; s < kOzS; ++s) {
     const float a = rintf(h);
     out[s * stride] = __float2bfloat16_rn(a);  // integer with |a| <= 256: exact
@@ -42,15 +48,16 @@ __device__ __forceinline__ void slice_value(df2 v, int e, __nv_bfloat16* out, in
     const float t = __fadd_rn(d, l);
     const float bb = __fsub_rn(t, d);
     const float err = __fadd_rn(__fsub_rn(d, __fsub_rn(t, bb)), __fsub_rn(l, bb));
-    h = ldexpf(t, 8);
-    l = ldexpf(err, 8);
+    h = t * 256.f;
+    l = err * 256.f;
   }
 }
 
 // The same slices as BF16 bit patterns in registers (for fragments built without shared
 // memory).
 __device__ __forceinline__ void slice_bits(df2 v, int e, unsigned short (&out)[kOzS]) {
-  float h = ldexpf(v.hi, 8 - e), l = ldexpf(v.lo, 8 - e);
+  const float sc = pow2f(8 - e);   // scaling by a power of two: exact
+  float h = v.hi * sc, l = v.lo * sc;
 #pragma unroll
   for (int s = 0; s < kOzS; ++s) {
     const float a = rintf(h);
@@ -59,8 +66,8 @@ __device__ __forceinline__ void slice_bits(df2 v, int e, unsigned short (&out)[k
     const float t = __fadd_rn(d, l);
     const float bb = __fsub_rn(t, d);
     const float err = __fadd_rn(__fsub_rn(d, __fsub_rn(t, bb)), __fsub_rn(l, bb));
-    h = ldexpf(t, 8);
-    l = ldexpf(err, 8);
+    h = t * 256.f;
+    l = err * 256.f;
   }
 }
 
