@@ -220,7 +220,10 @@ __device__ void flush_df(df2* G, const df2* Ap, const df2* Bp, int m, int N, int
 // per-output slicing and scaling outweigh a 16-term double-float sum. For k = 32 at N = 256 a
 // version that re-sliced P per n-tile took 1198 ms against 625 ms for the SIMT fold.
 constexpr int kTcFlushMaxK = 16;
-constexpr int kTcFlushMinN = 65;
+#ifndef NMC_TC_FLUSH_MIN_N
+#define NMC_TC_FLUSH_MIN_N 65
+#endif
+constexpr int kTcFlushMinN = NMC_TC_FLUSH_MIN_N;
 
 // A fragment (row-major 16 x 16) of P rows r_lo / r_hi = r_lo + 8, k = k0..k0+15: register v
 // holds row (v & 1 ? r_hi : r_lo), k = k0 + 2tq + {0, 1} (+8 for v >= 2); the lower half of
