@@ -292,6 +292,41 @@ __device__ __forceinline__ void flush_store(df2* Gsp, const float (&acc)[kOzS][4
   }
 }
 
+// KS k-steps of 16 (m <= 16 KS): a warp slices a 16-row block of P once and sweeps it across
+// all 8-column n-tiles of its spin.
+template <int KS>
+__device__ __forceinline__ void flush_rows(df2* G, const df2* Ap, const df2* Bp, int m, int N,
+                                           int KK, long long NN, int ns, const int* sEr,
+                                           const int* sFc, int warp, int nw, int g, int tq,
+                                           int nb) {
+  for (int job = warp; job < ns * nb; job += nw) {
+    const int sp = job / nb, rb = job - sp * nb;
+    const int r_lo = rb * 16 + g;
+    const df2* A_ = Ap + sp * KK * N;
+    const df2* B_ = Bp + sp * KK * N;
+    const int* er = sEr + sp * N;
+    const int* fc = sFc + sp * N;
+    uint32_t af[KS][kOzS][4];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) flush_a_frag(af[k], A_, er, r_lo, 16 * k, m, N, tq);
+#pragma unroll 1
+    for (int cn = 0; cn < 2 * nb; ++cn) {
+      float acc[kOzS][4];
+#pragma unroll
+      for (int q = 0; q < kOzS; ++q)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[q][w] = 0.f;
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        uint32_t bf[kOzS][2];
+        flush_b_frag(bf, B_, fc, cn * 8 + g, 16 * k, m, N, tq);
+        flush_mma(acc, af[k], bf);
+      }
+      flush_store(G + sp * NN, acc, er, fc, r_lo, cn * 8, N, tq);
+    }
+  }
+}
+
 __device__ void flush_tc(df2* G, const df2* Ap, const df2* Bp, int m, int N, int KK,
                          long long NN, int ns, int* sEr, int* sFc) {
   for (int t = threadIdx.x; t < 2 * ns * N; t += blockDim.x) {
@@ -307,28 +342,12 @@ __device__ void flush_tc(df2* G, const df2* Ap, const df2* Bp, int m, int N, int
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int g = lane >> 2, tq = lane & 3;
   const int nb = (N + 15) >> 4;
-  // one k-step (m <= 16): a warp slices a 16-row block of P once and sweeps it across all
-  // 8-column n-tiles
-  for (int job = warp; job < ns * nb; job += nw) {
-    const int sp = job / nb, rb = job - sp * nb;
-    const int r_lo = rb * 16 + g;
-    uint32_t af[kOzS][4];
-    flush_a_frag(af, Ap + sp * KK * N, sEr + sp * N, r_lo, 0, m, N, tq);
-#pragma unroll 1
-    for (int cn = 0; cn < 2 * nb; ++cn) {
-      uint32_t bf[kOzS][2];
-      flush_b_frag(bf, Bp + sp * KK * N, sFc + sp * N, cn * 8 + g, 0, m, N, tq);
-      float acc[kOzS][4];
-#pragma unroll
-      for (int q = 0; q < kOzS; ++q)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) acc[q][w] = 0.f;
-      flush_mma(acc, af, bf);
-      flush_store(G + sp * NN, acc, sEr + sp * N, sFc + sp * N, r_lo, cn * 8, N, tq);
-    }
-  }
+  flush_rows<1>(G, Ap, Bp, m, N, KK, NN, ns, sEr, sFc, warp, nw, g, tq, nb);   // m <= 16
 }
 
+// TC: fold on the tensor cores (flush_tc) instead of the double-float loop (flush_df); a
+// separate instantiation, so the FP32-pipe variant keeps its smaller register footprint.
+template <bool TC>
 __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_accept[2];  // by attempt parity: see the loop
@@ -350,7 +369,6 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
   int8_t* sl = (int8_t*)(udf + N);
   int* sEr = (int*)(((uintptr_t)(sl + N) + 15) & ~(uintptr_t)15);   // flush scales
   int* sFc = sEr + ns * N;
-  const bool tc_flush = KK <= kTcFlushMaxK && N >= kTcFlushMinN;
 
   df2* Gg = f.G + (long long)c * ns * NN;
   df2* G = f.g_in_smem ? Gs : Gg;
@@ -455,7 +473,7 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
       ++m;
       __syncthreads();
       if (m == KK) {
-        if (tc_flush) flush_tc(G, Ap, Bp, m, N, KK, NN, ns, sEr, sFc);
+        if constexpr (TC) flush_tc(G, Ap, Bp, m, N, KK, NN, ns, sEr, sFc);
         else flush_df(G, Ap, Bp, m, N, KK, NN, ns);
         m = 0;
         __syncthreads();
@@ -468,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
     }
   }
   if (m > 0) {
-    if (tc_flush) flush_tc(G, Ap, Bp, m, N, KK, NN, ns, sEr, sFc);
+    if constexpr (TC) flush_tc(G, Ap, Bp, m, N, KK, NN, ns, sEr, sFc);
     else flush_df(G, Ap, Bp, m, N, KK, NN, ns);
     __syncthreads();
   }
@@ -507,8 +525,13 @@ template void flip_slice<float>(const FlipArgs<float>&, int, cudaStream_t);
 template <>
 void flip_slice<df2>(const FlipArgs<df2>& f, int n_chains, cudaStream_t st) {
   const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(df2), f.g_in_smem, f.ns);
-  allow_max_dynamic_smem((const void*)k_flip_df);
-  k_flip_df<<<n_chains, kThreads, bytes, st>>>(f);
+  if (f.kk <= kTcFlushMaxK && f.N >= kTcFlushMinN) {
+    allow_max_dynamic_smem((const void*)k_flip_df<true>);
+    k_flip_df<true><<<n_chains, kThreads, bytes, st>>>(f);
+  } else {
+    allow_max_dynamic_smem((const void*)k_flip_df<false>);
+    k_flip_df<false><<<n_chains, kThreads, bytes, st>>>(f);
+  }
 }
 
 }  // namespace nmc
