@@ -62,10 +62,9 @@ TRAFFIC = {
     # dram__bytes_read.sum,dram__bytes_write.sum (cold cache): 16.90-16.93 MB read, 0 written
     # -- the chain operand once, no re-reads
     "gemm_oz.cu": ("07d20475a96cca7b", 16.92e6),
-    # k_flip_df, same configuration (one slice of 256 chains x 2 spins): 16.90 MB read
-    # (G as FP32 pairs, once), 0 written (source hash taken after a preprocessor-only edit
-    # that leaves the compiled kernel unchanged)
-    "flip.cu": ("d06b30f3530e048f", 16.90e6),
+    # k_flip_df<false> (the FP32-pipe fold used at N = 64), same configuration (one slice of
+    # 256 chains x 2 spins): 16.86-16.88 MB read (G as FP32 pairs, once), <= 3.6 KB written
+    "flip.cu": ("6e801840cba3a655", 16.87e6),
 }
 
 
