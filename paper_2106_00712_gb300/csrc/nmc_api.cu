@@ -9,6 +9,9 @@
 //    for l in block, descending: wrap G <- B_l^{-1} G B_l, flip slice l
 //    left stack L_j = L_{j+1} B_block (held as L^T = U D T), recompute (I + R_j L_j)^{-1}
 // Stack slots 1..nb-1 hold R_j or L_j; slot 0 (R_0) and slot nb (L_nb) are the identity.
+// A sweep ends with an update of three device counters (Philox sweep counter, measurement
+// slot, drift-history slot) that the kernels read, so a sweep of each direction can be
+// recorded once as a CUDA graph and replayed (sweep_graph).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
