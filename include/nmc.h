@@ -16,7 +16,7 @@
  *  - The caller owns every buffer it passes; the library copies what it needs. The
  *    library owns the context and all device memory it allocates (stream-ordered
  *    cudaMallocAsync on the context stream), except nmc_green_noalloc, which allocates none.
- *  - Lattices: nmc_lattice (square or honeycomb). The generator of network initialization
+ *  - Lattices: the nmc_lattice enum, square or honeycomb. The generator of network initialization
  *    (Algorithm 1, steps 2-3) has its own header, nmc_gen.h; nmc_generate mode 1 uses it.
  *  - Device work is ordered on the context's CUDA stream (nmc_options.cuda_stream, NULL =
  *    the legacy default stream). Calls that return host data synchronise that stream.
