@@ -52,3 +52,16 @@ def test_convergence_criterion():
     assert nimc_run._converged_at(curve([1.5, 1.4]), "x", ref) is None
     # the reference's own error widens the band
     assert nimc_run._converged_at(curve([1.019], err=0.0), "x", (1.0, 0.02)) == 1
+
+
+def test_table2_golden_fixture():
+    """The printed Table 2 values the honeycomb GPU test compares against (tests/golden)."""
+    path = os.path.join(ROOT, "tests", "golden", "table2_honeycomb_L6.txt")
+    rows = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        q, *v = line.split()
+        rows[q] = [float(x) for x in v]
+    assert rows["E_k"] == [-1.360, 0.004, -1.357, 0.003, -1.358, 0.001]
+    assert rows["S_Gamma"] == [3.11, 0.10, 2.99, 0.10, 3.00, 0.04]

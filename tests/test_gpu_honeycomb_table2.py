@@ -13,12 +13,28 @@ combined standard errors. E_k agrees within one standard error of the paper's va
 longer runs; S(Gamma) comes out about 4% low (2.87-2.88, +-0.012), which is within the
 5-sigma bar used here.
 """
+import os
+
 import pytest
 
 pytestmark = pytest.mark.gpu
 
-EK, EK_ERR = -1.358, 0.001
-SG, SG_ERR = 3.00, 0.04
+
+def _golden():
+    """Table 2 values from tests/golden/table2_honeycomb_L6.txt: {quantity: {column: (m, e)}}."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_honeycomb_L6.txt")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        q, *v = line.split()
+        v = [float(x) for x in v]
+        out[q] = {"dqmc_train": (v[0], v[1]), "nimc": (v[2], v[3]), "good_dqmc": (v[4], v[5])}
+    return out
+
+
+EK, EK_ERR = _golden()["E_k"]["good_dqmc"]
+SG, SG_ERR = _golden()["S_Gamma"]["good_dqmc"]
 
 
 @pytest.fixture(scope="module")
