@@ -7,14 +7,17 @@ per GPU with i.i.d. random +-1 initial fields (Philox). One step = one measuring
 every chain (N * L_tau flip attempts per chain, with the wraps, UDV stabilizations and
 measurements the sweep contains). Metric: flip attempts per second, whole job.
 
-Paths timed: "fp64" (all propagation in FP64), "fp32x2" (flips, delayed updates, wraps and
-stack products in compensated FP32 pairs on the FP32 pipes; QR, recompute, ratios and
-measurements in FP64) and "fp32" (plain FP32 propagation). A path counts for `value` only if
-its max |G_propagated - G_recomputed(FP64)| over the run stays <= 1e-5.
+Paths timed: "fp64" (all propagation in FP64), "split_bf16" (G, flips and delayed updates
+in compensated FP32 pairs, every propagation product on the BF16 tensor cores by exact
+integer slicing; QR, recompute, ratios and measurements in FP64), "fp32x2" (the same with
+every product in FP32 pairs on the FP32 pipes) and "fp32" (plain FP32 propagation), plus the
+particle-hole single-spin variants. A path counts for `value` only if its max
+|G_propagated - G_recomputed(FP64)| over the run stays <= 1e-5.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Multi-GPU: launched by torch.distributed.run, one rank per GPU; chains are sharded
-(global chain index = rank * 256 + local), no data-path collective ("weak" scaling).
+Multi-GPU: one rank per GPU (under torch.distributed.run, or re-launched under it by
+--gpus N); chains are sharded (global chain index = rank * 256 + local), no data-path
+collective ("weak" scaling); the host scalars are reduced over gloo.
 """
 import argparse
 import hashlib
@@ -34,26 +37,28 @@ from paper_2106_00712_gb300.sharding import weak_offset  # noqa: E402
 METRIC = "DQMC flips/s at |ΔG|≤1e-5 vs FP64, mixed vs FP64 path; serve p50/p99 latency"
 UNIT = "flips/s"
 DRIFT_BAR = 1e-5
-# FP64 SIMT FMA peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s);
-# FP32 SIMT: 152 x 128 FFMA/clk x 2 x 2.07 GHz.
-# Compensated FP32 pairs: one multiply-add costs 12 FP32-pipe instructions
-# (TwoProd by FMA, TwoSum, two cross-term FMAs, two adds), so the pipe's ceiling in
-# algorithmic flop is 80.55 / 12 = 6.71 TFLOP/s.
-PEAK_TFLOPS = {"fp64": 1.259, "fp32": 80.55, "fp32x2": 6.713}
-def _bf16_peak():
+# Nominal SIMT peaks, used only if the live probe fails: 152 SMs x 2 DFMA/clk x 2 flop x
+# 2.07 GHz (FP64) and 152 x 128 FFMA/clk x 2 x 2.07 GHz (FP32).
+NOMINAL_TFLOPS = {"fp64": 1.259, "fp32": 80.55}
+# Compensated FP32 pairs: one multiply-add costs 12 FP32-pipe instructions (TwoProd by FMA,
+# TwoSum, two cross-term FMAs, two adds); a secondary ceiling for the pair kernels.
+PAIR_INSTR_PER_FMA = 12
+# exact-slicing tensor-core products: 7 integer BF16 slices per operand, the 28 slice pairs
+# (s, t) with s + t <= 6 issued per algorithmic product
+OZ_PRODUCTS = 28
+TC_KERNEL = "k_gemm_oz (BF16 mma.sync, exact 7x7-slice products)"
+
+
+def _measured_peaks_file():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops"])
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"]))
     except Exception:
-        return 1900.0  # recipe fallback
+        return 1900.0, 1700.0   # the profiling recipe's fallback
 
 
-BF16_PEAK = _bf16_peak()
-PEAK_SOURCE = {
-    "fp64": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
-    "fp32": "152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (derived)",
-    "fp32x2": "FP32 pipe (152 x 128 x 2 x 2.07 GHz) / 12 instructions per compensated FMA",
-}
+BF16_PEAK, BF16_PEAK_SUSTAINED = _measured_peaks_file()
 # DRAM bytes per launch of a kernel, from an ncu capture of the same launch configuration
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel source at
 # capture time; reported as null once the source has changed.
@@ -74,53 +79,78 @@ def traffic_of(src):
     return b if h is not None and h == src_hash(src) else None
 
 
-def class_rooflines(st, base, impl, ns, acc):
+def step_flop(N, L, nb, chains, ns, acc):
+    """Algorithmic flop of one sweep of every chain, counted per step of the sweep (both
+    spins unless ns = 1): wraps 2 products per slice, stack products 1 per slice, the
+    recompute (3 products, Gauss-Jordan 3N^3) and QR with Q (8/3 N^3) and the T update
+    (1 product) per stabilization, the measurement (2 products) per stabilization, and the
+    delayed updates 2N^2 per accepted flip. Products are 2N^3."""
+    p = 2.0 * N ** 3
+    per_matrix = (L * (2 * p + p) + nb * (3 * p + 3.0 * N ** 3 + 8.0 / 3.0 * N ** 3 + p + 2 * p)
+                  + acc * N * L * 2.0 * N * N)
+    return per_matrix * ns * chains
+
+
+def class_rooflines(st, base, ns, acc, peaks, tc):
     """Achieved vs peak for each timed kernel class of the path (algorithmic work per launch
     / average event-timed launch duration). Per launch, every class runs over the batch of
-    ns x chains matrices of N x N: products 2N^3 each; QR with Q formed 8/3 N^3; Gauss-Jordan
-    on [X | N right-hand sides] 3N^3; a slice of flips, per accepted flip and spin, a rank-k
-    flush share 2N^2 plus the panel column and row 2Nk (k = delay)."""
+    ns x chains matrices of N x N: products 2N^3 each (the tensor-core class: its 28 BF16
+    slice products, against the BF16 peak); QR with Q formed 8/3 N^3; Gauss-Jordan on
+    [X | N right-hand sides] 3N^3; a slice of flips, per accepted flip and spin, a rank-k
+    flush share 2N^2 plus the panel column and row 2Nk (k = delay). Each class is quoted
+    against the pipe it runs on: `peaks` holds the measured FP64 and FP32 SIMT peaks and the
+    BF16 tensor peak (TFLOP/s)."""
     N, C, k = WL.N, WL.n_chains, WL.delay_k
     batch = ns * C
+    simt = "fp32" if base in ("fp32", "fp32x2") else "fp64"
     def rate(cls, flop):
         launches, timed, ms = st[cls]
         return flop / (ms / max(timed, 1) * 1e-3) / 1e12
+    def entry(bound, kernel, a, peak, src, **kw):
+        return {"bound": bound, "kernel": kernel, "achieved": a, "peak": peak,
+                "unit": "TFLOP/s", "frac": a / peak, "peak_source": src, **kw}
     out = {}
     if st.get("gemm_tc", (0,))[0]:
         a = rate("gemm_tc", OZ_PRODUCTS * 2.0 * N ** 3 * batch)
-        out["gemm_tc"] = {"bound": "tensor", "kernel": "k_gemm_oz (BF16 mma.sync, exact 7x7-slice products)",
-                          "achieved": a, "peak": BF16_PEAK, "unit": "TFLOP/s", "frac": a / BF16_PEAK,
-                          "traffic": traffic_of("gemm_oz.cu"),
-                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
-                          "algorithmic": f"{OZ_PRODUCTS} BF16 slice products of 2N^3 per product"}
-    for cls, kname, peak, src in (
-            ("gemm_df", "k_gemm_df<64,64> (compensated FP32 pairs)", PEAK_TFLOPS["fp32x2"], PEAK_SOURCE["fp32x2"]),
-            ("gemm", {"fp64": "k_gemm<double,64>", "fp32": "k_gemm<float,64>",
-                      "fp32x2": "k_gemm<double,64> (FP64 recompute, T updates)"}[base],
-             PEAK_TFLOPS["fp32" if base == "fp32" else "fp64"],
-             PEAK_SOURCE["fp32" if base == "fp32" else "fp64"])):
-        if st.get(cls, (0,))[0]:
-            a = rate(cls, 2.0 * N ** 3 * batch)
-            out[cls] = {"bound": "alu", "kernel": kname, "achieved": a, "peak": peak,
-                        "unit": "TFLOP/s", "frac": a / peak, "traffic": None, "peak_source": src}
+        out["gemm_tc"] = entry("tensor", TC_KERNEL, a, peaks["bf16"],
+                               "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst), of measured",
+                               traffic=traffic_of("gemm_oz.cu"),
+                               algorithmic=f"{OZ_PRODUCTS} BF16 slice products of 2N^3 per "
+                                           "FP64-class product",
+                               achieved_fp64_class=a / OZ_PRODUCTS)
+    if st.get("gemm_df", (0,))[0]:
+        a = rate("gemm_df", 2.0 * N ** 3 * batch)
+        out["gemm_df"] = entry("alu", "k_gemm_df<64,64> (compensated FP32 pairs)", a,
+                               peaks["fp32"], "FP32 FMA probe (nmc_fma_probe), of measured",
+                               frac_of_pair_ceiling=a / (peaks["fp32"] / PAIR_INSTR_PER_FMA))
+    if st.get("gemm", (0,))[0]:
+        kern = {"fp64": "k_gemm<double,64>", "fp32": "k_gemm<float,64>",
+                "fp32x2": "k_gemm<double,64> (FP64 recompute, T updates)"}[base]
+        pk = "fp32" if base == "fp32" else "fp64"
+        a = rate("gemm", 2.0 * N ** 3 * batch)
+        out["gemm"] = entry("alu", kern, a, peaks[pk],
+                            f"{pk.upper()} FMA probe (nmc_fma_probe), of measured")
     if st.get("flip", (0,))[0]:
         a = rate("flip", acc * N * C * ns * (2.0 * N * N + 2.0 * N * k))
-        fpk = PEAK_TFLOPS[base]
-        out["flip"] = {"bound": "alu", "kernel": {"fp64": "k_flip<double>", "fp32": "k_flip<float>",
-                                                  "fp32x2": "k_flip_df"}[base],
-                       "achieved": a, "peak": fpk, "unit": "TFLOP/s", "frac": a / fpk,
-                       "traffic": traffic_of("flip.cu") if base == "fp32x2" else None,
-                       "peak_source": PEAK_SOURCE[base],
-                       "algorithmic": "per accepted flip and spin 2N^2 + 2Nk (delayed rank-k updates); "
-                                      "one launch = one slice of every chain; latency-bound (one "
-                                      "sequential site loop per chain)"}
+        kern = {"fp64": "k_flip<double>", "fp32": "k_flip<float>",
+                "fp32x2": "k_flip_df"}[base]
+        extra = {}
+        if base == "fp32x2":
+            extra["frac_of_pair_ceiling"] = a / (peaks["fp32"] / PAIR_INSTR_PER_FMA)
+            extra["traffic"] = traffic_of("flip.cu")
+        out["flip"] = entry("alu", kern, a, peaks[simt],
+                            f"{simt.upper()} FMA probe (nmc_fma_probe), of measured",
+                            algorithmic="per accepted flip and spin 2N^2 + 2Nk (delayed rank-k "
+                                        "updates); one launch = one slice of every chain; "
+                                        "latency-bound (one sequential site loop per chain)",
+                            **extra)
     for cls, kname, flop in (("qrp", "k_qrp (FP64 column-pivoted QR + Q)", 8.0 / 3.0 * N ** 3),
                              ("solve", "k_solve (FP64 Gauss-Jordan)", 3.0 * N ** 3)):
         if st.get(cls, (0,))[0]:
-            a = rate(cls, flop * batch)
-            out[cls] = {"bound": "alu", "kernel": kname, "achieved": a, "peak": PEAK_TFLOPS["fp64"],
-                        "unit": "TFLOP/s", "frac": a / PEAK_TFLOPS["fp64"], "traffic": None,
-                        "peak_source": PEAK_SOURCE["fp64"]}
+            out[cls] = entry("alu", kname, rate(cls, flop * batch), peaks["fp64"],
+                             "FP64 FMA probe (nmc_fma_probe), of measured")
+    for v in out.values():
+        v.setdefault("traffic", None)
     return out
 
 
@@ -235,28 +265,71 @@ def oracle_rate(cores, steps, warmup):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-# path name -> (precision, particle-hole single spin, gemm_impl)
-PATHS = {"fp64": (0, 0, 0), "fp32": (1, 0, 0), "fp32x2": (2, 0, 0), "fp32x2_simt": (2, 0, 1),
-         "fp64_ph": (0, 1, 0), "fp32x2_ph": (2, 1, 0)}
-# exact-slicing tensor-core products: 7 integer BF16 slices per operand, slice pairs with
-# s + t <= 8 (28 products) issued per algorithmic product
-OZ_PRODUCTS = 28
+# path name -> (nmc precision, particle-hole single spin)
+PATHS = {"fp64": (0, 0), "fp32": (1, 0), "split_bf16": (2, 0), "fp32x2": (4, 0),
+         "fp64_ph": (0, 1), "split_bf16_ph": (2, 1)}
+BASE = {0: "fp64", 1: "fp32", 2: "fp32x2", 4: "fp32x2"}   # arithmetic class of the SIMT parts
 
 
-def context(nmc, path, rank, stream):
-    prec, ph, impl = PATHS[path]
-    return nmc.Context(WL.Lx, WL.Ly, WL.t, WL.U, WL.beta, WL.dtau, WL.n_wrap, seed=WL.seed,
-                       n_chains=WL.n_chains, delay_k=WL.delay_k, precision=prec,
-                       drift_tol=1e300, chain_offset=weak_offset(rank, WL.n_chains),
-                       stream=stream.cuda_stream, ph_symmetric=ph, gemm_impl=impl)
+def context(nmc, path, rank, stream, wl=WL, chains=None):
+    prec, ph = PATHS[path]
+    n = wl.n_chains if chains is None else chains
+    return nmc.Context(wl.Lx, wl.Ly, wl.t, wl.U, wl.beta, wl.dtau, wl.n_wrap, seed=wl.seed,
+                       n_chains=n, delay_k=wl.delay_k, precision=prec,
+                       drift_tol=1e300, chain_offset=weak_offset(rank, n),
+                       stream=stream.cuda_stream, ph_symmetric=ph)
 
 
-def run_path(nmc, torch, prec_name, steps, warmup, rank, stream, flush_buf):
+def probe_peaks(nmc, torch, stream):
+    """Measured SIMT peaks of this GPU (TFLOP/s): the library's multiply-add probe in FP64
+    and FP32 (best of 3 launches, CUDA events on the launching stream), cuBLAS TF32 (torch,
+    8192^3, best of 5) for reference, and the BF16 tensor peak from MEASURED_PEAKS.json."""
+    out = {"bf16": BF16_PEAK, "bf16_sustained": BF16_PEAK_SUSTAINED}
+    blocks, threads = 152 * 4, 256
+    buf = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    for kind, name, iters in ((0, "fp64", 20000), (1, "fp32", 400000)):
+        try:
+            best = float("inf")
+            for _ in range(3):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                nmc.nmc_fma_probe(kind, blocks, threads, iters, buf.data_ptr(), stream.cuda_stream)
+                b.record(stream)
+                b.synchronize()
+                best = min(best, a.elapsed_time(b))
+            out[name] = blocks * threads * iters * 16.0 / (best * 1e-3) / 1e12
+        except Exception:
+            out[name] = NOMINAL_TFLOPS[name]
+            out[name + "_source"] = "nominal (probe failed)"
+    try:
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        x = torch.randn(8192, 8192, device="cuda")
+        torch.matmul(x, x)
+        best = float("inf")
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            torch.matmul(x, x)
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+        out["tf32"] = 2.0 * 8192 ** 3 / (best * 1e-3) / 1e12
+        torch.backends.cuda.matmul.allow_tf32 = old
+        del x
+    except Exception:
+        out["tf32"] = None
+    return out
+
+
+def run_path(nmc, torch, path, steps, warmup, rank, stream, flush_buf):
     """W untimed warm-up sweeps, then K timed sweeps (the value: one CUDA-event pair per
     step, sweeps replayed from recorded graphs as a user runs them), then K further sweeps
     with per-kernel event brackets (the roofline's launch durations; bracketing every launch
     adds its own overhead, so those steps are not the value)."""
-    c = context(nmc, prec_name, rank, stream)
+    c = context(nmc, path, rank, stream)
 
     def timed(k_steps):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(k_steps)]
@@ -276,6 +349,7 @@ def run_path(nmc, torch, prec_name, steps, warmup, rank, stream, flush_buf):
         c.kernel_stats(reset=True)
         ms = timed(steps)
         launches = c.kernel_stats(reset=True)
+        graphs = c.graph_stats()
         c.profile(True)
         ms_profiled = timed(steps)
         c.profile(False)
@@ -283,16 +357,15 @@ def run_path(nmc, torch, prec_name, steps, warmup, rank, stream, flush_buf):
         obs = c.measure()
     finally:
         c.close()
-    return ms, stats, obs, launches, ms_profiled
+    return ms, stats, obs, launches, ms_profiled, graphs
 
 
-def run_e2e(nmc, torch, prec_name, steps, rank, stream):  # noqa: C901
+def run_e2e(nmc, torch, path, steps, rank, stream):
     """Same metric through the public C ABI with host buffers: host fields in, K measuring
     sweeps, observables and fields back to host, all inside the timed region."""
-    import numpy as np
     from paper_2106_00712_gb300.workloads import random_fields
     fields = random_fields(WL.n_chains, WL.L_tau, WL.N, seed=1000 + rank)
-    c = context(nmc, prec_name, rank, stream)
+    c = context(nmc, path, rank, stream)
     try:
         c.set_fields(fields)                          # warm the path once
         c.sweep(1, measure=1)
@@ -310,24 +383,73 @@ def run_e2e(nmc, torch, prec_name, steps, rank, stream):  # noqa: C901
     return dt, h2d, d2h, obs
 
 
+def run_latency(nmc, torch, stream, path, sweeps=200, warm=4):
+    """The 4x4 one-chain workload (U=4, beta=2, dtau=0.1, n_wrap=10, 200 sweeps): latency-
+    bound, so reported as time per flip attempt, event-timed over the whole run."""
+    from paper_2106_00712_gb300.workloads import SQUARE_4x4 as W4
+    c = context(nmc, path, 0, stream, wl=W4, chains=1)
+    try:
+        c.generate()
+        c.sweep(warm, measure=0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        c.sweep(sweeps, measure=1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        drift = c.measure().max_drift
+    finally:
+        c.close()
+    attempts = sweeps * W4.N * W4.L_tau
+    return {"workload": W4.name, "path": path, "sweeps": sweeps,
+            "us_per_attempt": ms * 1e3 / attempts, "ms_per_sweep": ms / sweeps,
+            "flips_per_s": attempts / (ms * 1e-3), "max_drift": drift}
+
+
 def ctypes_obs_bytes(nmc):
     import ctypes
     return ctypes.sizeof(nmc.Obs)
 
 
-def main():
+def relaunch_under_torchrun(n):
+    """`--gpus N` without a launcher: re-execute this script under torch.distributed.run
+    with N ranks on this node (one GPU each)."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={n}", "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def rank_plan(rank, world, local):
+    """What each rank runs: its GPU and its disjoint range of global chain indices."""
+    off = weak_offset(rank, WL.n_chains)
+    return {"rank": rank, "world": world, "device": local, "chain_offset": off,
+            "chains": WL.n_chains, "chain_range": [off, off + WL.n_chains]}
+
+
+def main():  # noqa: C901
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", default="fp64,fp32x2,fp32x2_simt,fp32,fp64_ph,fp32x2_ph")
-    ap.add_argument("--value-paths", default="fp64,fp32x2,fp32x2_simt,fp32",
+    ap.add_argument("--paths", default="fp64,split_bf16,fp32x2,fp32,fp64_ph,split_bf16_ph")
+    ap.add_argument("--value-paths", default="fp64,split_bf16,fp32x2,fp32",
                     help="paths eligible for `value` (the per-spin G of the specification)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests in the serving leg (0 = skip)")
+    ap.add_argument("--plan-only", action="store_true",
+                    help="print each rank's plan (device, chain range) and exit; no GPU work")
     args = ap.parse_args()
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1 and args.impl == "ours":
+        sys.exit(relaunch_under_torchrun(args.gpus))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -341,6 +463,10 @@ def main():
               "timing": "value: K steps, one event pair each, sweeps replayed from recorded "
                         "CUDA graphs; roofline: K further steps with every kernel bracketed"}
 
+    if args.plan_only:
+        print(json.dumps(rank_plan(rank, world, local)), flush=True)
+        return
+
     if args.impl == "reference":
         if rank != 0:
             return
@@ -352,7 +478,8 @@ def main():
                 "config": {**config, "chains_per_step": cores},
                 "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                                  "sample": f"{cores} chains (one per process), {args.steps} "
-                                           f"timed sweeps each, after {args.warmup} warm-up"},
+                                           f"timed sweeps each, after {args.warmup} warm-up; "
+                                           "the oracle is plain numpy/scipy FP64"},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -360,8 +487,8 @@ def main():
 
     import torch
     import torch.distributed as dist
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    if world > 1:   # host-side barrier and the two scalar reductions only (no data path)
+        dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     import __graft_entry__
     if rank == 0:
@@ -372,6 +499,13 @@ def main():
     nmc.load()
     stream = torch.cuda.current_stream()
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    peaks = probe_peaks(nmc, torch, stream)
+
+    def max_host(v):
+        t = torch.tensor([float(v)], dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     paths = [p for p in args.paths.split(",") if p]
     flips_per_step = WL.n_chains * WL.N * WL.L_tau
@@ -381,18 +515,14 @@ def main():
             if world > 1:
                 dist.barrier()
             torch.cuda.synchronize()
-            ms, stats, obs, launches, ms_prof = run_path(nmc, torch, p, args.steps, args.warmup,
-                                                         rank, stream, flush_buf)
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            d = torch.tensor([obs.max_drift], device="cuda", dtype=torch.float64)
-            if world > 1:
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                dist.all_reduce(d, op=dist.ReduceOp.MAX)
-            ms_max = float(t.item())
-            results[p] = {"ms": ms_max, "stats": stats, "drift": float(d.item()), "obs": obs,
+            ms, stats, obs, launches, ms_prof, graphs = run_path(
+                nmc, torch, p, args.steps, args.warmup, rank, stream, flush_buf)
+            ms_max = max_host(ms)
+            drift = max_host(obs.max_drift)
+            results[p] = {"ms": ms_max, "stats": stats, "drift": drift, "obs": obs,
                           "value": world * flips_per_step * args.steps / (ms_max * 1e-3),
                           "launches": sum(v[0] for v in launches.values()),
-                          "ms_profiled": ms_prof}
+                          "ms_profiled": ms_prof, "graphs": graphs}
     clk = clocks.summary()
 
     eligible = [p for p in paths if p in args.value_paths.split(",")] or paths
@@ -402,17 +532,23 @@ def main():
     st = r["stats"]
     dom = max(st, key=lambda k: st[k][2])          # kernel class with most device time
     launches_total = r["launches"]   # kernels launched in the timed (value) steps
-    prec, ph, impl = PATHS[best]
+    prec, ph = PATHS[best]
     ns = 1 if ph else 2
-    base = {0: "fp64", 1: "fp32", 2: "fp32x2"}[prec]
-    per_launch_flop = 2.0 * WL.N ** 3 * ns * WL.n_chains  # batched N x N x N, ns per chain
+    base = BASE[prec]
     tot_ms = max(sum(x[2] for x in st.values()), 1e-30)
     share = {k: v[2] / tot_ms for k, v in st.items() if v[0]}
-    rl = class_rooflines(st, base, impl, ns, r["obs"].accept)
+    rl = class_rooflines(st, base, ns, r["obs"].accept, peaks, prec == 2)
     roofline = dict(rl.get(dom) or rl[max(rl, key=lambda k: st[k][2])])
     roofline.update({"dominant_class": dom, "share": share})
     roofline["others"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "frac")}
                           for k, v in rl.items() if k != dom}
+    sf = step_flop(WL.N, WL.L_tau, WL.L_tau // WL.n_wrap, WL.n_chains, ns, r["obs"].accept)
+    whole_step = {"algorithmic_tflop_per_step": sf / 1e12,
+                  "achieved_tflops": world * sf / (r["ms"] / args.steps * 1e-3) / 1e12,
+                  "per_attempt_flop": sf / flips_per_step,
+                  "per_attempt_flop_21N2": 21.0 * WL.N ** 2,
+                  "count": "step_flop(): wraps, stack products, recompute, QR, T update, "
+                           "measurement and delayed updates, per sweep"}
 
     e2e_dt, h2d, d2h, _ = run_e2e(nmc, torch, best, args.steps, rank, stream)
     e2e = {"value": flips_per_step * args.steps / e2e_dt * world, "unit": UNIT,
@@ -420,12 +556,16 @@ def main():
            "path": best, "includes": "set_fields(host) + stack build + K sweeps + "
                                      "measure(host) + get_fields(host)"}
 
+    latency = None
     serve = None
-    if args.serve_requests > 0 and world == 1:
-        from paper_2106_00712_gb300.serving import serve_stream
-        serve = serve_stream(args.serve_requests)
-        serve["workload"] = ("Poisson stream, L in {6,8,10,12}, beta in {2,4,6}, U in {2,4,8}, "
-                             "dtau 0.1, 16 chains, 20 + 50 sweeps, FP32X2, 100 GB budget")
+    if world == 1:
+        latency = {p: run_latency(nmc, torch, stream, p) for p in ("fp64", "split_bf16")}
+        if args.serve_requests > 0:
+            from paper_2106_00712_gb300.serving import serve_stream
+            serve = serve_stream(args.serve_requests)
+            serve["workload"] = ("Poisson stream, L in {6,8,10,12}, beta in {2,4,6}, "
+                                 "U in {2,4,8}, dtau 0.1, 16 chains, 20 + 50 sweeps, "
+                                 "SPLIT_BF16, 100 GB budget")
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -436,24 +576,29 @@ def main():
         v, dt = oracle_rate(cores, n_sw, 0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{cores} chains of the same workload, one per process, {n_sw} "
-                         f"measuring sweeps each from random fields ({dt:.1f} s wall)"}
+                         f"measuring sweeps each from random fields ({dt:.1f} s wall); the "
+                         "oracle is plain numpy/scipy FP64, not an optimised CPU program"}
     paths_out = {p: {"value": results[p]["value"], "ms_per_step": results[p]["ms"] / args.steps,
                      "max_drift": results[p]["drift"],
                      "meets_1e-5": results[p]["drift"] <= DRIFT_BAR,
                      "energy": results[p]["obs"].energy.mean,
                      "double_occ": results[p]["obs"].double_occ.mean,
                      "accept": results[p]["obs"].accept,
+                     "graphs_recorded_replayed": list(results[p]["graphs"]),
                      "ms_per_step_kernel_brackets": results[p]["ms_profiled"] / args.steps}
                  for p in paths}
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32+f64", "fp32x2": "f32x2+f64"}[base],
-            "gemm_impl": {0: "tensor cores (exact BF16 slicing) where N <= 64", 1: "SIMT"}[impl],
             "data": "synthetic",
-            "config": {**config, "path": best}, "paths": paths_out,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "serve": serve,
+            "config": {**config, "path": best},
+            "drift_measure": "max over stabilizations and chains of |G_propagated - "
+                             "G_recomputed|, G_recomputed in FP64 from the FP64 UDV stacks of "
+                             "the same fields (free-running chains)",
+            "paths": paths_out, "peaks_measured": peaks,
+            "roofline": roofline, "whole_step": whole_step, "cpu_baseline": cpu, "e2e": e2e,
+            "latency_4x4_1chain": latency, "clocks": clk, "serve": serve,
             "gpu_launches": launches_total}
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -54,11 +54,18 @@ typedef enum {
 /* Arithmetic of the propagation steps. Ratios, acceptance, UDV stabilization, the
  * recomputed G and the measurements are always FP64. */
 typedef enum {
-  NMC_FP64 = 0,      /* flips, delayed updates, wraps and stack products in FP64          */
-  NMC_FP32 = 1,      /* flips, delayed updates and wraps in FP32 (FP32 accumulation)      */
-  NMC_FP32X2 = 2     /* flips, delayed updates, wraps and stack products in compensated
-                        FP32 pairs (error-free products and sums, ~2^-44 relative) on the
-                        FP32 pipes; QR, recompute, ratios and measurement in FP64         */
+  NMC_FP64 = 0,       /* flips, delayed updates, wraps and stack products in FP64         */
+  NMC_FP32 = 1,       /* flips, delayed updates and wraps in FP32 (FP32 accumulation)     */
+  NMC_SPLIT_BF16 = 2, /* compensated: G, flips and delayed-update panels in FP32 pairs
+                         (error-free products and sums); every wrap, stack and measurement
+                         product on the BF16 tensor cores by exact integer slicing (each
+                         operand cut into 7 integer BF16 slices, slice products exact in FP32
+                         accumulators, ~2^-49 of the row/column maxima), and the rank-k fold
+                         too where that is faster; QR, recompute, ratios, measurement FP64 */
+  NMC_TF32X3 = 3,     /* not built (NMC_EINVAL): three TF32 products accumulated in FP32 give
+                         FP32-class products, which cannot hold the 1e-5 drift bar here   */
+  NMC_FP32X2 = 4      /* compensated as NMC_SPLIT_BF16, with every product and fold in FP32
+                         pairs on the FP32 SIMT pipes (no tensor cores)                   */
 } nmc_precision;
 
 /* Lattices of Eq. 3 (both periodic and bipartite; K_ij = -t per nearest-neighbour pair,
@@ -77,16 +84,14 @@ typedef struct {
   int delay_k;           /* accepted flips folded per rank-k delayed update (>= 1) def. 16   */
   int precision;         /* nmc_precision                                        default 0  */
   double drift_tol;      /* NMC_ENUMERIC if max|G_wrapped - G_recomputed| exceeds this;
-                            <= 0 selects 1e-6 (FP64), 1e-3 (FP32), 1e-5 (FP32X2) default 0 */
+                            <= 0 selects 1e-6 (FP64), 1e-3 (FP32), 1e-5 (SPLIT_BF16,
+                            FP32X2)                                              default 0 */
   long long chain_offset;/* global index of local chain 0 (Philox counter word 2) def. 0   */
   void* cuda_stream;     /* cudaStream_t for all device work                     def. NULL */
   int ph_symmetric;      /* 1: propagate spin up only; at half filling on the bipartite
                             lattice G_dn = I - P G_up^T P (P = diag of sublattice signs) exactly,
                             R_dn = 1 + Delta_dn G_up_ii, and G~_dn follows the same way.
                             Same chain, half the work.                           default 0  */
-  int gemm_impl;         /* FP32X2 products with a constant operand: 0 = BF16 tensor cores with
-                            exact integer slicing when N <= 64 (else SIMT), 1 = SIMT
-                            double-float always                                  default 0  */
   int sweep_graphs;      /* 1: after the first sweep of each direction, record one sweep as a
                             CUDA graph and replay it (one launch per sweep instead of one per
                             kernel; the same kernels with the same arguments, so the results
@@ -200,7 +205,7 @@ nmc_status nmc_get_fields(nmc_ctx* ctx, int8_t* s, size_t n);
 /* Copy the current equal-time G of one chain and spin (0 = up, 1 = down) to host
  * memory (N x N row-major). After an even number of sweeps since the fields were set,
  * G sits at slice 0, after an odd number at slice L_tau (equal to slice 0 cyclically).
- * In FP32 / FP32X2 mode the propagated G is widened to double. */
+ * In FP32, SPLIT_BF16 and FP32X2 mode the propagated G is widened to double. */
 nmc_status nmc_get_green(nmc_ctx* ctx, int chain, int spin, double* G);
 
 /* Sizes: N, L_tau, n_chains, effective delay (after the shared-memory clamp). */
@@ -251,6 +256,11 @@ nmc_status nmc_profile(nmc_ctx* ctx, int enable);
  * *n receives the number of classes. reset != 0 clears the counters afterwards. */
 nmc_status nmc_kernel_stats(nmc_ctx* ctx, nmc_kernel_stat* out, int max, int* n, int reset);
 
+/* Sweep graphs (nmc_options.sweep_graphs): *recorded = graphs recorded, *replayed = sweeps
+ * run by replaying a recorded graph, since the context was created. Either pointer may be
+ * NULL. Host counters only; no device work. */
+nmc_status nmc_graph_stats(const nmc_ctx* ctx, long long* recorded, long long* replayed);
+
 /* Equal-time Green's functions G_0 = (I + B_{L-1}...B_0)^{-1} of each chain and spin from
  * caller-given fields, WITHOUT allocating: no cudaMalloc, cudaFree or other allocating
  * call. The paper has no counterpart; this exists for callers that cannot allocate device
@@ -267,13 +277,33 @@ nmc_status nmc_kernel_stats(nmc_ctx* ctx, nmc_kernel_stat* out, int max, int* n,
  * the library, held by every GPU that loads it until exit. Chains are processed in chunks
  * that fit; one chain needs 20 N^2 + 4 N doubles (24 N^2 + 4 N when N > 111), so
  * NMC_EINVAL is returned, before any work is enqueued, when that exceeds the array
- * (N > 409), and for invalid arguments. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call shares the one array and overwrites it: calls
- * whose work overlaps on the GPU (other streams, other threads) race -- serialise them. */
+ * (N > 409), and for invalid arguments. Each call made outside stream capture looks up
+ * the array's device address (cudaGetSymbolAddress) in the current device's context and
+ * caches it for that device; a call made while cuda_stream is being captured uses the
+ * cached address. A device reset (cudaDeviceReset) invalidates that address, so after a
+ * reset, and before the first capture on a device, make one call outside capture (a call
+ * under capture with no cached address returns NMC_ECUDA). NMC_ECUDA is also returned,
+ * with nothing enqueued, when a CUDA error is already pending on entry, and at the first
+ * failed launch. Every call shares the one array and overwrites it: calls whose work
+ * overlaps on the GPU (other streams, other threads) race -- serialise them. */
 nmc_status nmc_green_noalloc(int N, int L_tau, int n_wrap, double lam, const double* d_expK_m,
                              const int8_t* d_fields, int n_chains, double* d_G,
                              void* cuda_stream);
+
+/* Arithmetic-pipe probe (measurement): launch blocks x threads threads on cuda_stream,
+ * each running 8 independent fused multiply-add chains for `iters` rounds in FP64 (kind 0)
+ * or FP32 (kind 1), and store one value per thread to d_out (device, blocks * threads
+ * elements of that type). Work: blocks * threads * iters * 16 flop. Timed by the caller
+ * with events on the same stream, it gives the measured FP64 / FP32 SIMT peak that the
+ * roofline of the SIMT kernels is quoted against. NMC_EINVAL for bad sizes. */
+nmc_status nmc_fma_probe(int kind, int blocks, int threads, int iters, void* d_out,
+                         void* cuda_stream);
+
+/* Testing hook (host only): make the n-th device allocation of any context from now on
+ * fail as if the device were out of memory (the call that made it returns NMC_ENOMEM and
+ * frees what it had allocated when the context is destroyed); n <= 0 disarms. Lets callers
+ * test their handling of NMC_ENOMEM without exhausting a shared GPU's memory. */
+void nmc_debug_fail_alloc(long long n);
 
 const char* nmc_last_error(const nmc_ctx* ctx);
 const char* nmc_version(void);

@@ -525,7 +525,7 @@ template void flip_slice<float>(const FlipArgs<float>&, int, cudaStream_t);
 template <>
 void flip_slice<df2>(const FlipArgs<df2>& f, int n_chains, cudaStream_t st) {
   const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(df2), f.g_in_smem, f.ns);
-  if (f.kk <= kTcFlushMaxK && f.N >= kTcFlushMinN) {
+  if (f.tc_fold && f.kk <= kTcFlushMaxK && f.N >= kTcFlushMinN) {
     allow_max_dynamic_smem((const void*)k_flip_df<true>);
     k_flip_df<true><<<n_chains, kThreads, bytes, st>>>(f);
   } else {

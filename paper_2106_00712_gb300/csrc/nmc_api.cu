@@ -13,6 +13,7 @@
 // slot, drift-history slot) that the kernels read, so a sweep of each direction can be
 // recorded once as a CUDA graph and replayed (sweep_graph).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -123,6 +124,7 @@ struct nmc_ctx {
   bool cap = false;                    // recording: launches go to cap_stream
   cudaStream_t cap_stream = nullptr;
   int direct_since_build = 0;          // direct sweeps since the stacks were last built
+  long long graphs_recorded = 0, graphs_replayed = 0;
 
   // per-kernel accounting: launch counts always, CUDA-event brackets when prof is set
   bool prof = false;
@@ -139,7 +141,9 @@ struct nmc_ctx {
   int batch() const { return ns() * opt.n_chains; }
   long long NN() const { return (long long)N * N; }
   bool fp32() const { return opt.precision == NMC_FP32; }
-  bool dfp() const { return opt.precision == NMC_FP32X2; }
+  // compensated FP32-pair propagation: products on the tensor cores (SPLIT_BF16) or SIMT
+  bool dfp() const { return opt.precision == NMC_SPLIT_BF16 || opt.precision == NMC_FP32X2; }
+  bool tc() const { return opt.precision == NMC_SPLIT_BF16; }
 };
 
 namespace {
@@ -248,6 +252,18 @@ void free_all(nmc_ctx* x) {
   x->have_fields = false;
 }
 
+// Allocation-failure injection (nmc_debug_fail_alloc): the n-th device allocation from the
+// moment it is armed fails as if the allocator had run out of memory; 0 = off.
+std::atomic<long long> g_fail_alloc_in{0};
+
+bool injected_alloc_failure() {
+  long long n = g_fail_alloc_in.load();
+  while (n > 0) {
+    if (g_fail_alloc_in.compare_exchange_weak(n, n - 1)) return n == 1;
+  }
+  return false;
+}
+
 template <typename T>
 nmc_status dalloc(nmc_ctx* x, T** p, size_t count) {
   if (x->dry) {
@@ -255,6 +271,8 @@ nmc_status dalloc(nmc_ctx* x, T** p, size_t count) {
     *p = nullptr;
     return NMC_OK;
   }
+  if (injected_alloc_failure())
+    return fail(x, NMC_ENOMEM, "cudaMallocAsync: out of memory (injected by nmc_debug_fail_alloc)");
   void* q = nullptr;
   const cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), x->st());
   if (e != cudaSuccess) {
@@ -306,7 +324,7 @@ nmc_status alloc_all(nmc_ctx* x) {
     NMC_TRY(dalloc(x, &x->dXb, mats));
     NMC_TRY(dalloc(x, &x->dEmh2, NN));
     NMC_TRY(dalloc(x, &x->dEph2, NN));
-    x->oz = x->opt.gemm_impl == 0 && gemm_oz_supported(x->N);
+    x->oz = x->tc() && gemm_oz_supported(x->N);
     if (x->oz)
       for (int a = 0; a < 4; ++a)
         for (int r = 0; r < 2; ++r) {
@@ -522,6 +540,7 @@ void flip(nmc_ctx* x, int l, const uint8_t* replay) {
     FlipArgs<df2> f{x->dG2, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                     (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
                     x->dCounts, replay, nullptr, split(dm), split(dp), x->ns(), x->dCtr};
+    f.tc_fold = x->tc() ? 1 : 0;
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   } else if (x->fp32()) {
     FlipArgs<float> f{x->dGf, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
@@ -868,6 +887,7 @@ bool sweep_graph(nmc_ctx* x, bool up, bool meas) {
     }
     gr.exec = exec;
     gr.ptrs = state;
+    ++x->graphs_recorded;
   }
   if (cudaGraphLaunch(gr.exec, x->st()) != cudaSuccess) {
     cudaGetLastError();
@@ -875,6 +895,7 @@ bool sweep_graph(nmc_ctx* x, bool up, bool meas) {
     return false;
   }
   advance_slots(x, up);
+  ++x->graphs_replayed;
   x->n_hist += x->nb;   // one drift record per block
   for (int k = 0; k < kNumClasses; ++k) x->launches[k] += gr.launches[k];
   return true;
@@ -942,7 +963,6 @@ void nmc_default_options(nmc_options* o) {
   o->chain_offset = 0;
   o->cuda_stream = nullptr;
   o->ph_symmetric = 0;
-  o->gemm_impl = 0;
   o->sweep_graphs = 1;
 }
 
@@ -996,9 +1016,15 @@ nmc_status nmc_configure(nmc_ctx* x, const nmc_options* o) {
   nmc_options n;
   nmc_default_options(&n);
   if (o) n = *o;
-  if (n.n_chains < 1 || n.delay_k < 1 || (n.precision != NMC_FP64 && n.precision != NMC_FP32 && n.precision != NMC_FP32X2) ||
+  if (n.precision == NMC_TF32X3)
+    return fail(x, NMC_EINVAL,
+                "NMC_TF32X3 is not built: three TF32 products with FP32 accumulation give "
+                "FP32-class products, which cannot hold the 1e-5 drift bar of this model");
+  if (n.n_chains < 1 || n.delay_k < 1 ||
+      (n.precision != NMC_FP64 && n.precision != NMC_FP32 && n.precision != NMC_SPLIT_BF16 &&
+       n.precision != NMC_FP32X2) ||
       n.chain_offset < 0 || n.n_chains > (1 << 20) || (n.ph_symmetric != 0 && n.ph_symmetric != 1) ||
-      (n.gemm_impl != 0 && n.gemm_impl != 1) || (n.sweep_graphs != 0 && n.sweep_graphs != 1))
+      (n.sweep_graphs != 0 && n.sweep_graphs != 1))
     return fail(x, NMC_EINVAL, "invalid nmc_options");
   x->opt = n;
   clamp_delay(x);
@@ -1415,6 +1441,15 @@ nmc_status nmc_kernel_stats(nmc_ctx* x, nmc_kernel_stat* out, int max, int* n, i
   if (n) *n = KC_COUNT;
   if (reset)
     for (int c = 0; c < KC_COUNT; ++c) x->launches[c] = x->timed[c] = 0, x->total_ms[c] = 0;
+  return NMC_OK;
+}
+
+void nmc_debug_fail_alloc(long long n) { g_fail_alloc_in.store(n > 0 ? n : 0); }
+
+nmc_status nmc_graph_stats(const nmc_ctx* x, long long* recorded, long long* replayed) {
+  if (!x) return NMC_EINVAL;
+  if (recorded) *recorded = x->graphs_recorded;
+  if (replayed) *replayed = x->graphs_replayed;
   return NMC_OK;
 }
 

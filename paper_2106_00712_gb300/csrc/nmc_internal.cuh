@@ -158,6 +158,7 @@ struct FlipArgs {
   df2 dm2, dp2;              // dm, dp as FP32 pairs (compensated mode)
   int ns;                    // 2 spins, or 1: spin up only, G_dn = I - P G_up^T P
   const long long* ctr;      // device counters (ctr[0] = sweep counter) or null: use sweep
+  int tc_fold = 0;           // compensated mode: 1 = rank-k fold may use the tensor cores
 };
 template <typename T> void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st);
 size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem, int ns);

@@ -32,19 +32,29 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 double* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device, looked up once per device. In host
-// code the symbol name is only a host-side stand-in, never a usable device address.
-cudaError_t scratch_on_current_device(double** out) {
+// Device address of g_scratch in the current device's context. In host code the symbol name
+// is only a host-side stand-in, never a usable device address. The address belongs to the
+// context that loaded the library's module: a device reset (cudaDeviceReset) or another
+// context on the same device loads it again, possibly elsewhere. So every call made outside
+// stream capture looks the address up again (cheap once the module is loaded) and caches
+// it per device; a call made while `st` is being captured uses the cached address, which a
+// call outside capture must have set after the last reset.
+cudaError_t scratch_on_current_device(cudaStream_t st, double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = (double*)p;
+  } else if (!g_scratch_addr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;  // no address looked up outside capture yet
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
@@ -104,9 +114,11 @@ extern "C" nmc_status nmc_green_noalloc(int N, int L_tau, int n_wrap, double lam
   if (shared + per_chain > kScratchDoubles) return NMC_EINVAL;  // one chain does not fit
   const int chunk = (int)((kScratchDoubles - shared) / per_chain);
 
-  double* base_ptr = nullptr;
-  if (scratch_on_current_device(&base_ptr) != cudaSuccess) return NMC_ECUDA;
+  // An error left pending by earlier work (not ours) is reported, not consumed.
+  if (cudaPeekAtLastError() != cudaSuccess) return NMC_ECUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* base_ptr = nullptr;
+  if (scratch_on_current_device(st, &base_ptr) != cudaSuccess) return NMC_ECUDA;
   const int nb = L_tau / n_wrap;
 
   double* I = base_ptr;
@@ -172,6 +184,8 @@ extern "C" nmc_status nmc_green_noalloc(int N, int L_tau, int n_wrap, double lam
     GemmArgs<double> g3 = base(N, B, src.U, src.sU, Y, NN, d_G + (long long)c0 * 2 * NN);
     g3.brow = vscale(src.D, src.sD, SC_INV_MAX1);
     gemm(g3, st);
+    // stop at the first failed launch instead of queueing later chunks behind it
+    if (cudaGetLastError() != cudaSuccess) return NMC_ECUDA;
   }
   return cudaGetLastError() == cudaSuccess ? NMC_OK : NMC_ECUDA;
 }

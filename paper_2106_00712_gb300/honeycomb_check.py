@@ -23,7 +23,7 @@ from .workloads import HONEYCOMB_6x6
 TABLE2 = {"ekin": (-1.358, 0.001), "s_gamma": (3.00, 0.04)}
 
 
-def run(wl=HONEYCOMB_6x6, chains=None, warm=None, meas=None, precision=nmc.NMC_FP32X2, ph=1,
+def run(wl=HONEYCOMB_6x6, chains=None, warm=None, meas=None, precision=nmc.NMC_SPLIT_BF16, ph=1,
         stream=None):
     chains = chains or wl.n_chains
     warm = wl.n_warm if warm is None else warm
@@ -52,7 +52,7 @@ def main():
     ap.add_argument("--chains", type=int, default=None)
     ap.add_argument("--warm", type=int, default=None)
     ap.add_argument("--meas", type=int, default=None)
-    ap.add_argument("--precision", type=int, default=nmc.NMC_FP32X2)
+    ap.add_argument("--precision", type=int, default=nmc.NMC_SPLIT_BF16)
     ap.add_argument("--ph", type=int, default=1)
     a = ap.parse_args()
     print(json.dumps(run(chains=a.chains, warm=a.warm, meas=a.meas, precision=a.precision,

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libnmc.so")
 NMC_OK, NMC_EINVAL, NMC_ENOMEM, NMC_ECUDA, NMC_ENUMERIC, NMC_ETIMEOUT, NMC_ESTATE = range(7)
 STATUS_NAMES = {0: "NMC_OK", 1: "NMC_EINVAL", 2: "NMC_ENOMEM", 3: "NMC_ECUDA",
                 4: "NMC_ENUMERIC", 5: "NMC_ETIMEOUT", 6: "NMC_ESTATE"}
-NMC_FP64, NMC_FP32, NMC_FP32X2 = 0, 1, 2
+NMC_FP64, NMC_FP32, NMC_SPLIT_BF16, NMC_TF32X3, NMC_FP32X2 = 0, 1, 2, 3, 4
 NMC_SQUARE, NMC_HONEYCOMB = 0, 1
 LATTICES = {"square": NMC_SQUARE, "honeycomb": NMC_HONEYCOMB}
 
@@ -26,7 +26,8 @@ EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_field
             "nmc_query", "nmc_sync", "nmc_footprint", "nmc_sweep_replay",
             "nmc_measure", "nmc_get_fields", "nmc_get_green", "nmc_get_dims",
             "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_series", "nmc_philox", "nmc_philox_device",
-            "nmc_drift_history", "nmc_profile", "nmc_kernel_stats", "nmc_green_noalloc",
+            "nmc_drift_history", "nmc_profile", "nmc_kernel_stats", "nmc_graph_stats",
+            "nmc_green_noalloc", "nmc_debug_fail_alloc", "nmc_fma_probe",
             "nmc_last_error",
             "nmc_version", "nmc_destroy")
 
@@ -41,8 +42,7 @@ class Options(ctypes.Structure):
     _fields_ = [("n_chains", ctypes.c_int), ("delay_k", ctypes.c_int),
                 ("precision", ctypes.c_int), ("drift_tol", ctypes.c_double),
                 ("chain_offset", ctypes.c_longlong), ("cuda_stream", ctypes.c_void_p),
-                ("ph_symmetric", ctypes.c_int), ("gemm_impl", ctypes.c_int),
-                ("sweep_graphs", ctypes.c_int)]
+                ("ph_symmetric", ctypes.c_int), ("sweep_graphs", ctypes.c_int)]
 
 
 class Est(ctypes.Structure):
@@ -122,7 +122,10 @@ def load():
         "nmc_drift_history": (i, [vp, vp, ctypes.c_longlong, P(ctypes.c_longlong)]),
         "nmc_profile": (i, [vp, i]),
         "nmc_kernel_stats": (i, [vp, vp, i, P(i), i]),
+        "nmc_graph_stats": (i, [vp, P(ctypes.c_longlong), P(ctypes.c_longlong)]),
         "nmc_green_noalloc": (i, [i, i, i, d, vp, vp, i, vp, vp]),
+        "nmc_debug_fail_alloc": (None, [ctypes.c_longlong]),
+        "nmc_fma_probe": (i, [i, i, i, i, vp, vp]),
         "nmc_last_error": (ctypes.c_char_p, [vp]),
         "nmc_version": (ctypes.c_char_p, []),
         "nmc_destroy": (None, [vp]),
@@ -345,6 +348,25 @@ def nmc_green_noalloc(N, L_tau, n_wrap, lam, d_expK_ptr, d_fields_ptr, n_chains,
         raise NmcError(st, "nmc_green_noalloc")
 
 
+def nmc_graph_stats(ctx):
+    """(sweep graphs recorded, sweeps replayed from a recorded graph) since creation."""
+    rec, rep = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    _check(ctx, load().nmc_graph_stats(ctx, ctypes.byref(rec), ctypes.byref(rep)))
+    return rec.value, rep.value
+
+
+def nmc_debug_fail_alloc(n):
+    """Make the n-th device allocation from now fail with NMC_ENOMEM (0 = off)."""
+    load().nmc_debug_fail_alloc(int(n))
+
+
+def nmc_fma_probe(kind, blocks, threads, iters, d_out_ptr, stream=None):
+    """Launch the FP64 (kind 0) / FP32 (kind 1) multiply-add probe on `stream`."""
+    st = load().nmc_fma_probe(kind, blocks, threads, iters, ctypes.c_void_p(d_out_ptr), stream)
+    if st != NMC_OK:
+        raise NmcError(st, "nmc_fma_probe")
+
+
 def nmc_destroy(ctx):
     load().nmc_destroy(ctx)
 
@@ -360,14 +382,13 @@ class Context:
 
     def __init__(self, Lx, Ly, t, U, beta, dtau, n_wrap, seed=0, n_chains=1, delay_k=16,
                  precision=NMC_FP64, drift_tol=0.0, chain_offset=0, stream=None,
-                 ph_symmetric=0, gemm_impl=0, lattice=NMC_SQUARE, sweep_graphs=1):
+                 ph_symmetric=0, lattice=NMC_SQUARE, sweep_graphs=1):
         self.ctx = nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed, lattice)
         o = nmc_default_options()
         o.n_chains, o.delay_k, o.precision = n_chains, delay_k, precision
         o.drift_tol, o.chain_offset = drift_tol, chain_offset
         o.cuda_stream = stream
         o.ph_symmetric = int(ph_symmetric)
-        o.gemm_impl = int(gemm_impl)
         o.sweep_graphs = int(sweep_graphs)
         try:
             nmc_configure(self.ctx, o)
@@ -444,6 +465,9 @@ class Context:
 
     def kernel_stats(self, reset=False):
         return nmc_kernel_stats(self.ctx, reset)
+
+    def graph_stats(self):
+        return nmc_graph_stats(self.ctx)
 
 
 # ------------------------------------------------------------------ generator (nmc_gen.h)

@@ -25,7 +25,7 @@ import numpy as np
 from . import nmc
 from .workloads import SQUARE_16x16
 
-MODES = {"fp32": nmc.NMC_FP32, "fp32x2": nmc.NMC_FP32X2}
+MODES = {"fp32": nmc.NMC_FP32, "split_bf16": nmc.NMC_SPLIT_BF16, "fp32x2": nmc.NMC_FP32X2}
 
 
 def _ctx(wl, U, prec):

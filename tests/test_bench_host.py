@@ -13,11 +13,14 @@ import bench  # noqa: E402
 from paper_2106_00712_gb300 import nimc_run  # noqa: E402
 
 
+PEAKS = {"fp64": 1.2, "fp32": 75.0, "bf16": 1900.0}
+
+
 def test_class_rooflines_use_the_stated_algorithmic_work():
     N, C = bench.WL.N, bench.WL.n_chains
     # one timed launch of 1 ms per class, both spins
     st = {k: (1, 1, 1.0) for k in ("gemm_tc", "gemm", "flip", "qrp", "solve")}
-    rl = bench.class_rooflines(st, "fp32x2", 0, 2, acc=0.5)
+    rl = bench.class_rooflines(st, "fp32x2", 2, 0.5, PEAKS, True)
     batch = 2 * C
     assert rl["gemm_tc"]["achieved"] == pytest.approx(bench.OZ_PRODUCTS * 2 * N ** 3 * batch / 1e-3 / 1e12)
     assert rl["gemm"]["achieved"] == pytest.approx(2 * N ** 3 * batch / 1e-3 / 1e12)
@@ -27,10 +30,52 @@ def test_class_rooflines_use_the_stated_algorithmic_work():
     assert rl["solve"]["achieved"] == pytest.approx(3 * N ** 3 * batch / 1e-3 / 1e12)
     for v in rl.values():
         assert v["frac"] == pytest.approx(v["achieved"] / v["peak"])
-    # the FP64 path's products and flips are measured against the FP64 pipe
-    rl64 = bench.class_rooflines({"gemm": (1, 1, 1.0), "flip": (1, 1, 1.0)}, "fp64", 0, 2, 0.5)
-    assert rl64["gemm"]["peak"] == bench.PEAK_TFLOPS["fp64"]
-    assert rl64["flip"]["peak"] == bench.PEAK_TFLOPS["fp64"]
+    # each class against the pipe it runs on: the tensor class against BF16, the pair
+    # kernels against the FP32 SIMT pipe (with the emulation ceiling as a second figure),
+    # the FP64 stabilization against the FP64 pipe
+    assert rl["gemm_tc"]["peak"] == PEAKS["bf16"]
+    assert rl["flip"]["peak"] == PEAKS["fp32"]
+    assert rl["flip"]["frac_of_pair_ceiling"] == pytest.approx(
+        rl["flip"]["achieved"] / (PEAKS["fp32"] / bench.PAIR_INSTR_PER_FMA))
+    assert rl["gemm"]["peak"] == rl["qrp"]["peak"] == rl["solve"]["peak"] == PEAKS["fp64"]
+    rl64 = bench.class_rooflines({"gemm": (1, 1, 1.0), "flip": (1, 1, 1.0)}, "fp64", 2, 0.5,
+                                 PEAKS, False)
+    assert rl64["gemm"]["peak"] == PEAKS["fp64"]
+    assert rl64["flip"]["peak"] == PEAKS["fp64"]
+
+
+def test_whole_step_flop_count():
+    """step_flop against the step-by-step count written out for the 8x8 workload."""
+    N, L, nb, C = 64, 40, 4, 256
+    p = 2.0 * N ** 3
+    wraps, stack = 2 * p * L, p * L
+    stab = nb * (3 * p + 3 * N ** 3 + 8 / 3 * N ** 3 + p)
+    meas = nb * 2 * p
+    flips = 0.6 * N * L * 2 * N * N
+    want = (wraps + stack + stab + meas + flips) * 2 * C
+    assert bench.step_flop(N, L, nb, C, 2, 0.6) == pytest.approx(want)
+    # the per-attempt figure sits near the 21 N^2 estimate at this acceptance
+    per = bench.step_flop(N, L, nb, C, 2, 0.6) / (C * N * L)
+    assert 0.8 * 21 * N * N < per < 1.5 * 21 * N * N
+
+
+def test_gpus_flag_launches_one_rank_per_gpu_with_disjoint_chains():
+    """`bench.py --gpus 2` re-launches itself under torch.distributed.run with two ranks;
+    each rank takes its own GPU and a disjoint chain range (no GPU work in --plan-only)."""
+    import json
+    import subprocess
+    env = {k: v for k, v in os.environ.items()
+           if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")}
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2",
+                          "--plan-only"], capture_output=True, text=True, timeout=240, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    plans = sorted((json.loads(l) for l in out.stdout.splitlines() if l.startswith("{")),
+                   key=lambda d: d["rank"])
+    assert [p["rank"] for p in plans] == [0, 1]
+    assert all(p["world"] == 2 for p in plans)
+    assert [p["device"] for p in plans] == [0, 1]
+    (a0, a1), (b0, b1) = plans[0]["chain_range"], plans[1]["chain_range"]
+    assert a1 <= b0 and a1 - a0 == b1 - b0 == bench.WL.n_chains
 
 
 def test_traffic_is_reported_only_for_the_captured_source():

@@ -8,10 +8,14 @@ antiferromagnetic structure factor with opposite signs on the two sublattices, t
 the spin n_up - n_dn (4x the library's s = (n_up - n_dn)/2 estimator), normalised by the
 site count. The library's estimators use the symmetric-Trotter Green's function.
 
-A shorter run than the paper's (independent chains from random fields); the bar is a few
-combined standard errors. E_k agrees within one standard error of the paper's value in
-longer runs; S(Gamma) comes out about 4% low (2.87-2.88, +-0.012), which is within the
-5-sigma bar used here.
+A shorter run than the paper's (independent chains from random fields). Both quantities
+are held to the same bar, 3 combined standard errors. E_k agrees within one standard error
+of the paper's value in longer runs. S(Gamma) does not: long runs give 2.870(12) (FP64:
+2.891(24)), about 3 of the paper's standard errors below 3.00(4), and the cause is not
+found -- the paper names neither its honeycomb torus, nor the imaginary-time position of
+its estimator, nor the normalization that turns its printed S(Gamma) into a spin
+correlation sum. So that comparison is marked as an expected failure, not passed by a
+wider bar.
 """
 import os
 
@@ -48,13 +52,19 @@ def result():
     return honeycomb_check.run(chains=512, warm=150, meas=60)
 
 
+BAR = 3.0   # combined standard errors
+
+
 def test_kinetic_energy_matches_table2(result):
     m, e = result["ekin"]
-    assert abs(m - EK) < 4 * (EK_ERR ** 2 + e ** 2) ** 0.5, result["ekin"]
+    assert abs(m - EK) < BAR * (EK_ERR ** 2 + e ** 2) ** 0.5, result["ekin"]
     assert result["max_drift"] <= 1e-5
+    assert abs(result["density"][0] - 1.0) < 1e-12
 
 
+@pytest.mark.xfail(strict=False, reason=(
+    "4 S(Gamma) = 2.870(12) in long runs vs the printed 3.00(4); unresolved reading of the "
+    "paper's honeycomb torus, estimator position and S normalization"))
 def test_structure_factor_matches_table2(result):
     m, e = result["s_gamma_x4"]
-    assert abs(m - SG) < 5 * (SG_ERR ** 2 + e ** 2) ** 0.5, result["s_gamma_x4"]
-    assert abs(result["density"][0] - 1.0) < 1e-12
+    assert abs(m - SG) < BAR * (SG_ERR ** 2 + e ** 2) ** 0.5, result["s_gamma_x4"]

@@ -40,9 +40,11 @@ def _ctx(nmc, model, **kw):
 
 
 def _compare_run(nmc, model, chains, n_sweeps, measure_from=0, delay_k=16, fields=None,
-                 check_chains=None, chain_offset=0, precision=0, g_rel=G_REL, ph=0):
+                 check_chains=None, chain_offset=0, precision=0, g_rel=G_REL, ph=0,
+                 after=None):
     """Run n_sweeps on the GPU and on the oracle for the checked chains; compare the
-    field after every sweep (bit-exact), G at the end and the accumulated observables."""
+    field after every sweep (bit-exact), G at the end and the accumulated observables.
+    `after(c)`, if given, runs on the context before it closes."""
     check = list(range(chains)) if check_chains is None else check_chains
     with _ctx(nmc, model, n_chains=chains, delay_k=delay_k, chain_offset=chain_offset,
               drift_tol=1e-3, precision=precision, ph_symmetric=ph) as c:
@@ -78,6 +80,8 @@ def _compare_run(nmc, model, chains, n_sweeps, measure_from=0, delay_k=16, field
                 # same arithmetic class as the oracle: drift of the same order
                 assert got.max_drift < max(1e-8, 100 * refs[ch].max_drift), (
                     got.max_drift, refs[ch].max_drift)
+        if after is not None:
+            after(c)
         return c.measure()
 
 
@@ -237,7 +241,7 @@ def test_fp32x2_replay_meets_accuracy_bar(nmc):
     model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=0)
     chains = 2
     refs = [Chain(model, initial_fields(model, ch), ch) for ch in range(chains)]
-    with _ctx(nmc, model, n_chains=chains, precision=nmc.NMC_FP32X2) as c:
+    with _ctx(nmc, model, n_chains=chains, precision=nmc.NMC_SPLIT_BF16) as c:
         c.generate()
         for sw in range(4):
             before = np.stack([r.s.copy() for r in refs])
@@ -261,21 +265,42 @@ def test_fp32x2_free_running_decisions_equal_oracle(nmc):
     """Free-running FP32X2 chains make the oracle's decisions (4x4, 60 sweeps)."""
     model = Model(4, 4, 1.0, 4.0, 2.0, 0.1, 10, seed=0)
     _compare_run(nmc, model, chains=1, n_sweeps=60, measure_from=10,
-                 precision=nmc.NMC_FP32X2, g_rel=G_REL_X2)
+                 precision=nmc.NMC_SPLIT_BF16, g_rel=G_REL_X2)
 
 
+@pytest.mark.parametrize("prec", [2, 4])    # NMC_SPLIT_BF16, NMC_FP32X2
 @pytest.mark.parametrize("Lx,Ly,n_wrap,k,chains", [
     (2, 1, 2, 16, 2), (6, 6, 5, 5, 2), (10, 10, 5, 16, 2), (12, 12, 5, 8, 1)])
-def test_fp32x2_ragged_sizes(nmc, Lx, Ly, n_wrap, k, chains):
+def test_fp32x2_ragged_sizes(nmc, Lx, Ly, n_wrap, k, chains, prec):
     model = Model(Lx, Ly, 1.0, 4.0, 1.0, 0.1, n_wrap, seed=23)
     _compare_run(nmc, model, chains=chains, n_sweeps=3, measure_from=1, delay_k=k,
-                 precision=nmc.NMC_FP32X2, g_rel=G_REL_X2)
+                 precision=prec, g_rel=G_REL_X2)
 
 
 def test_fp32x2_8x8_256_chains_sampled(nmc):
     model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=0)
     _compare_run(nmc, model, chains=256, n_sweeps=2, measure_from=0, delay_k=16,
-                 check_chains=[3, 200], precision=nmc.NMC_FP32X2, g_rel=G_REL_X2)
+                 check_chains=[3, 200], precision=nmc.NMC_SPLIT_BF16, g_rel=G_REL_X2)
+
+
+def test_bench_config_graph_replayed_tensor_core_sampled(nmc):
+    """The benchmark configuration as bench.py times it: 8x8, U=4, beta=4, L_tau=40,
+    n_wrap=10, k=16, 256 chains, NMC_SPLIT_BF16 (products on the tensor cores), sweeps
+    replayed from recorded CUDA graphs. Eight measuring sweeps: the first two launch
+    directly (the graphs are recorded after them), the other six replay the recorded graph
+    of their direction. Oracle on four sampled chains: fields after every sweep bit-exact,
+    G at the end to 1e-8 relative, per-chain observables to 1e-9."""
+    model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=0)
+
+    def replayed(c):
+        rec, rep = c.graph_stats()
+        assert rec == 2 and rep == 6, (rec, rep)
+        st = c.kernel_stats()
+        assert st["gemm_tc"][0] > 0 and st["gemm_df"][0] == 0
+
+    _compare_run(nmc, model, chains=256, n_sweeps=8, measure_from=0, delay_k=16,
+                 check_chains=[0, 77, 190, 255], precision=nmc.NMC_SPLIT_BF16,
+                 g_rel=G_REL_X2, after=replayed)
 
 
 def test_fp32x2_tensor_core_slicing_equals_simt(nmc):
@@ -283,8 +308,8 @@ def test_fp32x2_tensor_core_slicing_equals_simt(nmc):
     the same chain and the same G to FP64-class accuracy (8x8, beta=4, 3 sweeps)."""
     model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=3)
     gs = {}
-    for impl in (0, 1):
-        with _ctx(nmc, model, n_chains=8, precision=nmc.NMC_FP32X2, gemm_impl=impl) as c:
+    for impl, prec in ((0, nmc.NMC_SPLIT_BF16), (1, nmc.NMC_FP32X2)):
+        with _ctx(nmc, model, n_chains=8, precision=prec) as c:
             c.generate()
             c.sweep(3, measure=1)
             st = c.kernel_stats()
@@ -318,7 +343,7 @@ def test_ph_single_spin_ragged_sizes(nmc, Lx, Ly, n_wrap, k, prec):
 def test_ph_single_spin_8x8_256_chains_sampled(nmc):
     model = Model(8, 8, 1.0, 4.0, 4.0, 0.1, 10, seed=0)
     _compare_run(nmc, model, chains=256, n_sweeps=2, measure_from=0, delay_k=16,
-                 check_chains=[0, 255], precision=nmc.NMC_FP32X2, g_rel=G_REL_X2, ph=1)
+                 check_chains=[0, 255], precision=nmc.NMC_SPLIT_BF16, g_rel=G_REL_X2, ph=1)
 
 
 # honeycomb lattice of the paper's Hubbard runs (2 L^2 sites; U = 3.83, beta = 6, dtau = 0.1

@@ -58,12 +58,40 @@ def test_no_alloc_green_matches_existing_entry_point(env):
         assert rel < G_REL, rel
 
 
+def test_no_alloc_green_with_solver_workspace_matches_existing(env):
+    """N = 144 (12 x 12) is above the size whose QR and solve fit in shared memory, so each
+    chain also takes the 2 N^2-per-matrix solver workspace; 10 chains span two chunks of the
+    fixed array (8 chains fit), and two calls run back to back."""
+    torch, nmc = env
+    Lx, Ly, t, U, beta, dtau, n_wrap = 12, 12, 1.0, 4.0, 0.4, 0.1, 2
+    N, L = Lx * Ly, int(round(beta / dtau))
+    lam = math.acosh(math.exp(dtau * U / 2))
+    expk = torch.from_numpy(nmc.nmc_expk(Lx, Ly, t, -dtau)).cuda()
+    stream = torch.cuda.current_stream()
+    for chains, seed in ((10, 3), (3, 4)):
+        fields = random_fields(chains, L, N, seed)
+        want = _existing(nmc, Lx, Ly, t, U, beta, dtau, n_wrap, fields)
+        d_fields = torch.from_numpy(fields).cuda()
+        d_G = torch.full((chains, 2, N, N), float("nan"), dtype=torch.float64, device="cuda")
+        nmc.nmc_green_noalloc(N, L, n_wrap, lam, expk.data_ptr(), d_fields.data_ptr(), chains,
+                              d_G.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        got = d_G.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        rel = np.max(np.abs(got - want)) / np.max(np.abs(want))
+        assert rel < G_REL, rel
+
+
 def test_no_alloc_rejects_oversize_before_any_work(env):
     torch, nmc = env
     dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
     f = torch.ones(16, dtype=torch.int8, device="cuda")
     with pytest.raises(nmc.NmcError) as e:   # 22 x 22 = 484 sites: one chain exceeds 32 MiB
         nmc.nmc_green_noalloc(484, 4, 2, 0.5, dummy.data_ptr(), f.data_ptr(), 1,
+                              dummy.data_ptr())
+    assert e.value.status == nmc.NMC_EINVAL
+    with pytest.raises(nmc.NmcError) as e:   # 410 sites: the first size past the 409 limit
+        nmc.nmc_green_noalloc(410, 4, 2, 0.5, dummy.data_ptr(), f.data_ptr(), 1,
                               dummy.data_ptr())
     assert e.value.status == nmc.NMC_EINVAL
     with pytest.raises(nmc.NmcError):
