@@ -43,10 +43,10 @@ NOMINAL_TFLOPS = {"fp64": 1.259, "fp32": 80.55}
 # Compensated FP32 pairs: one multiply-add costs 12 FP32-pipe instructions (TwoProd by FMA,
 # TwoSum, two cross-term FMAs, two adds); a secondary ceiling for the pair kernels.
 PAIR_INSTR_PER_FMA = 12
-# exact-slicing tensor-core products: 7 integer BF16 slices per operand, the 28 slice pairs
-# (s, t) with s + t <= 6 issued per algorithmic product
-OZ_PRODUCTS = 28
-TC_KERNEL = "k_gemm_oz (BF16 mma.sync, exact 7x7-slice products)"
+# exact-slicing tensor-core products: 6 BF16 slices per operand, the 21 slice pairs (s, t)
+# with s + t <= 5 issued per FP64-class product
+OZ_PRODUCTS = 21
+TC_KERNEL = "k_gemm_tc (tcgen05.mma kind::f16, TMEM accumulators, TMA-staged constant slices)"
 
 
 def _measured_peaks_file():
@@ -63,13 +63,6 @@ BF16_PEAK, BF16_PEAK_SUSTAINED = _measured_peaks_file()
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel source at
 # capture time; reported as null once the source has changed.
 TRAFFIC = {
-    # k_gemm_oz, bench launch configuration (512 products of 64 x 64), ncu --metrics
-    # dram__bytes_read.sum,dram__bytes_write.sum (cold cache): 16.90-16.93 MB read, 0 written
-    # -- the chain operand once, no re-reads
-    "gemm_oz.cu": ("07d20475a96cca7b", 16.92e6),
-    # k_flip_df<false> (the FP32-pipe fold used at N = 64), same configuration (one slice of
-    # 256 chains x 2 spins): 16.86-16.88 MB read (G as FP32 pairs, once), <= 3.6 KB written
-    "flip.cu": ("6e801840cba3a655", 16.87e6),
 }
 
 
@@ -114,7 +107,7 @@ def class_rooflines(st, base, ns, acc, peaks, tc):
         a = rate("gemm_tc", OZ_PRODUCTS * 2.0 * N ** 3 * batch)
         out["gemm_tc"] = entry("tensor", TC_KERNEL, a, peaks["bf16"],
                                "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst), of measured",
-                               traffic=traffic_of("gemm_oz.cu"),
+                               traffic=traffic_of("gemm_tc.cu"),
                                algorithmic=f"{OZ_PRODUCTS} BF16 slice products of 2N^3 per "
                                            "FP64-class product",
                                achieved_fp64_class=a / OZ_PRODUCTS)
@@ -285,9 +278,9 @@ def probe_peaks(nmc, torch, stream):
     and FP32 (best of 3 launches, CUDA events on the launching stream), cuBLAS TF32 (torch,
     8192^3, best of 5) for reference, and the BF16 tensor peak from MEASURED_PEAKS.json."""
     out = {"bf16": BF16_PEAK, "bf16_sustained": BF16_PEAK_SUSTAINED}
-    blocks, threads = 152 * 4, 256
+    blocks, threads = 152 * 8, 256
     buf = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
-    for kind, name, iters in ((0, "fp64", 20000), (1, "fp32", 400000)):
+    for kind, name, iters in ((0, "fp64", 10000), (1, "fp32", 200000)):
         try:
             best = float("inf")
             for _ in range(3):

@@ -305,6 +305,22 @@ nmc_status nmc_fma_probe(int kind, int blocks, int threads, int iters, void* d_o
  * test their handling of NMC_ENOMEM without exhausting a shared GPU's memory. */
 void nmc_debug_fail_alloc(long long n);
 
+/* Testing hook: one batched product of the compensated modes, as the sweep runs it, on host
+ * data (device memory is allocated and freed inside; synchronous). C[b] = cst X[b]
+ * (const_is_a = 1) or X[b] cst, for b < batch (even: matrix b belongs to chain b/2, spin
+ * b%2, sigma = +1 for spin 0 and -1 for spin 1). cst: N x N; X, C: [batch][N][N] row-major
+ * doubles; X is rounded to FP32 pairs first, as the sweep holds G. With `fields`
+ * (int8 [batch/2][N], +-1): the chain operand's element (r,c) is multiplied by
+ * e^{sigma lam (br s_r + bc s_c)} before the product and output element (r,c) by
+ * e^{sigma lam (cr s_r + cc s_c)} after it (br..cc in {-1,0,1}; br, bc only with the
+ * constant on the left, the one form the sweep uses). With `colscale`
+ * ([batch][N]): output column c of matrix b times colscale[b][c]. precision: NMC_SPLIT_BF16
+ * (tcgen05 tensor cores, exact slicing) or NMC_FP32X2 (FP32 pairs on the SIMT pipes).
+ * NMC_EINVAL for other arguments, NMC_ETIMEOUT if a bounded device wait expired. */
+nmc_status nmc_debug_product(int precision, int N, int batch, int const_is_a, const double* cst,
+                             const double* X, const int8_t* fields, int br, int bc, int cr,
+                             int cc, double lam, const double* colscale, double* C);
+
 const char* nmc_last_error(const nmc_ctx* ctx);
 const char* nmc_version(void);
 void nmc_destroy(nmc_ctx* ctx);

@@ -101,9 +101,13 @@ struct nmc_ctx {
   df2 *dG2 = nullptr, *dT12 = nullptr, *dEm2 = nullptr, *dEp2 = nullptr;
   df2 *dXa = nullptr, *dXb = nullptr, *dEmh2 = nullptr, *dEph2 = nullptr;
   // tensor-core slices of e^{-dtau K}, e^{+dtau K}, e^{-dtau K/2}, e^{+dtau K/2} as A / as B
+  // slices of e^{-dtau K}, e^{+dtau K}, e^{-dtau K/2}, e^{+dtau K/2} for the tcgen05 products,
+  // [constant][0: on the left, 1: on the right], their exponents and TMA tensor maps
   void* dOz[4][2] = {};
   int* dOzExp[4][2] = {};
+  alignas(64) unsigned char tmap[4][2][128] = {};
   bool oz = false;
+  int* dErr = nullptr;   // device flag: a bounded device-side wait expired (NMC_ETIMEOUT)
   std::vector<UDTBuf> slot;  // size nb + 1; entries 1..nb-1 allocated
   UDTBuf spare;
   double* dSign = nullptr;
@@ -236,6 +240,7 @@ void free_all(nmc_ctx* x) {
   for (int a = 0; a < 4; ++a)
     for (int r = 0; r < 2; ++r) x->dOz[a][r] = nullptr, x->dOzExp[a][r] = nullptr;
   x->oz = false;
+  x->dErr = nullptr;
   x->slot.clear();
   x->spare = UDTBuf{};
   x->dSign = nullptr;
@@ -324,14 +329,16 @@ nmc_status alloc_all(nmc_ctx* x) {
     NMC_TRY(dalloc(x, &x->dXb, mats));
     NMC_TRY(dalloc(x, &x->dEmh2, NN));
     NMC_TRY(dalloc(x, &x->dEph2, NN));
-    x->oz = x->tc() && gemm_oz_supported(x->N);
+    x->oz = x->tc();
+    if (x->oz && !x->dry && !gemm_tc_supported(x->N))
+      return fail(x, NMC_EINVAL, "NMC_SPLIT_BF16 needs N <= 320 and the TMA tensor-map encoder");
     if (x->oz)
       for (int a = 0; a < 4; ++a)
         for (int r = 0; r < 2; ++r) {
           uint16_t* p = nullptr;
-          NMC_TRY(dalloc(x, &p, oz_const_elems()));
+          NMC_TRY(dalloc(x, &p, tc_const_elems(x->N)));
           x->dOz[a][r] = p;
-          NMC_TRY(dalloc(x, &x->dOzExp[a][r], 64));
+          NMC_TRY(dalloc(x, &x->dOzExp[a][r], x->N));
         }
   }
   x->slot.assign(x->nb + 1, UDTBuf{});
@@ -350,10 +357,12 @@ nmc_status alloc_all(nmc_ctx* x) {
   x->hist_cap = 4096;
   NMC_TRY(dalloc(x, &x->dHist, x->hist_cap));
   NMC_TRY(dalloc(x, &x->dCtr, 3));
+  NMC_TRY(dalloc(x, &x->dErr, 1));
   if (x->dry) return NMC_OK;
 
   cudaStream_t st = x->st();
   NMC_CUDA(x, cudaMemsetAsync(x->dCtr, 0, 3 * sizeof(long long), st));
+  NMC_CUDA(x, cudaMemsetAsync(x->dErr, 0, sizeof(int), st));
   const size_t mb = NN * sizeof(double);
   NMC_CUDA(x, cudaMemcpyAsync(x->dK, x->hK.data(), mb, cudaMemcpyHostToDevice, st));
   NMC_CUDA(x, cudaMemcpyAsync(x->dEm, x->hEm.data(), mb, cudaMemcpyHostToDevice, st));
@@ -373,7 +382,9 @@ nmc_status alloc_all(nmc_ctx* x) {
     if (x->oz) {
       const double* src[4] = {x->dEm, x->dEp, x->dEmh, x->dEph};
       for (int a = 0; a < 4; ++a)
-        for (int r = 0; r < 2; ++r) slice_const(src[a], x->N, r, x->dOz[a][r], x->dOzExp[a][r], st);
+        for (int r = 0; r < 2; ++r)
+          if (!tc_prepare_const(src[a], x->N, r, x->dOz[a][r], x->dOzExp[a][r], x->tmap[a][r], st))
+            return fail(x, NMC_ECUDA, "cuTensorMapEncodeTiled failed for the constant's slices");
     }
   }
   NMC_CUDA(x, cudaGetLastError());
@@ -458,9 +469,10 @@ enum ConstId { OZ_EM = 0, OZ_EP = 1, OZ_EMH = 2, OZ_EPH = 3 };
 void df_gemm(nmc_ctx* x, DfGemmArgs& g, int const_id, bool const_is_a) {
   cudaStream_t st = x->st();
   if (x->oz) {
-    g.oz_const = x->dOz[const_id][const_is_a ? 0 : 1];
-    g.oz_const_exp = x->dOzExp[const_id][const_is_a ? 0 : 1];
-    launch(x, KC_GEMM_TC, [&] { gemm_oz(g, const_is_a, st); });
+    const int r = const_is_a ? 0 : 1;
+    g.oz_const = x->dOz[const_id][r];
+    g.oz_const_exp = x->dOzExp[const_id][r];
+    launch(x, KC_GEMM_TC, [&] { gemm_tc(g, const_is_a, x->tmap[const_id][r], x->dErr, st); });
   } else {
     launch(x, KC_GEMM_DF, [&] { gemm_df(g, st); });
   }
@@ -794,9 +806,17 @@ nmc_status ensure_series(nmc_ctx* x, long long need) {
 
 nmc_status check_drift(nmc_ctx* x) {
   std::vector<unsigned long long> bits(x->chains());
+  int err = 0;
   NMC_CUDA(x, cudaMemcpyAsync(bits.data(), x->dDrift, bits.size() * sizeof(unsigned long long),
                               cudaMemcpyDeviceToHost, x->st()));
+  NMC_CUDA(x, cudaMemcpyAsync(&err, x->dErr, sizeof(int), cudaMemcpyDeviceToHost, x->st()));
   NMC_CUDA(x, cudaStreamSynchronize(x->st()));
+  if (err) {
+    char buf[120];
+    std::snprintf(buf, sizeof buf, "a bounded device-side wait expired (tensor-core product, "
+                  "stage %d); results of this call are not valid", err);
+    return fail(x, NMC_ETIMEOUT, buf);
+  }
   double tol = x->opt.drift_tol;
   if (tol <= 0) tol = x->fp32() ? 1e-3 : x->dfp() ? 1e-5 : 1e-6;
   for (size_t c = 0; c < bits.size(); ++c) {
@@ -1445,6 +1465,94 @@ nmc_status nmc_kernel_stats(nmc_ctx* x, nmc_kernel_stat* out, int max, int* n, i
 }
 
 void nmc_debug_fail_alloc(long long n) { g_fail_alloc_in.store(n > 0 ? n : 0); }
+
+nmc_status nmc_debug_product(int precision, int N, int batch, int const_is_a, const double* cst,
+                             const double* X, const int8_t* fields, int br, int bc, int cr,
+                             int cc, double lam, const double* colscale, double* C) {
+  if ((precision != NMC_SPLIT_BF16 && precision != NMC_FP32X2) || N < 2 || N > 1024 ||
+      batch < 1 || batch % 2 || !cst || !X || !C || !(lam >= 0.0) ||
+      std::abs(br) > 1 || std::abs(bc) > 1 || std::abs(cr) > 1 || std::abs(cc) > 1 ||
+      (!const_is_a && (br || bc)))
+    return NMC_EINVAL;
+  const bool tc = precision == NMC_SPLIT_BF16;
+  if (tc && !gemm_tc_supported(N)) return NMC_EINVAL;
+  const size_t NN = (size_t)N * N, mats = NN * batch;
+  std::vector<void*> bufs;
+  auto dmalloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return p;
+  };
+  nmc_status st = NMC_OK;
+  double* dC64 = (double*)dmalloc(NN * sizeof(double));
+  df2* dC2 = (df2*)dmalloc(NN * sizeof(df2));
+  double* dX64 = (double*)dmalloc(mats * sizeof(double));
+  df2* dX2 = (df2*)dmalloc(mats * sizeof(df2));
+  double* dOut = (double*)dmalloc(mats * sizeof(double));
+  int8_t* dF = fields ? (int8_t*)dmalloc((size_t)(batch / 2) * N) : nullptr;
+  double* dCol = colscale ? (double*)dmalloc(mats / N * sizeof(double) * 1) : nullptr;
+  void* dSl = tc ? dmalloc(tc_const_elems(N) * 2) : nullptr;
+  int* dExp = tc ? (int*)dmalloc(N * sizeof(int)) : nullptr;
+  int* dErr = (int*)dmalloc(sizeof(int));
+  alignas(64) unsigned char tmap[128];
+  if (!dC64 || !dC2 || !dX64 || !dX2 || !dOut || (fields && !dF) || (colscale && !dCol) ||
+      (tc && (!dSl || !dExp)) || !dErr) {
+    cudaGetLastError();
+    st = NMC_ENOMEM;
+  }
+  if (st == NMC_OK) {
+    cudaMemcpy(dC64, cst, NN * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(dX64, X, mats * sizeof(double), cudaMemcpyHostToDevice);
+    if (fields) cudaMemcpy(dF, fields, (size_t)(batch / 2) * N, cudaMemcpyHostToDevice);
+    if (colscale) cudaMemcpy(dCol, colscale, mats / N * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemset(dErr, 0, sizeof(int));
+    split_to_df(dC64, dC2, (long long)NN, 0);
+    split_to_df(dX64, dX2, (long long)mats, 0);
+    DfGemmArgs g;
+    g.M = g.N = g.K = N;
+    g.batch = batch;
+    g.A = const_is_a ? dC2 : dX2; g.sA = const_is_a ? 0 : (long long)NN; g.lda = N;
+    g.B = const_is_a ? dX2 : dC2; g.sB = const_is_a ? (long long)NN : 0; g.ldb = N;
+    g.Cd = dOut; g.sC = (long long)NN; g.ldc = N;
+    g.colscale = dCol; g.sColscale = N;
+    g.fstride = N;
+    g.ns = 2;
+    if (fields) {
+      g.bfields = dF; g.br = br; g.bc = bc;
+      g.cfields = dF; g.cr = cr; g.cc = cc;
+    }
+    for (int m = -2; m <= 2; ++m) {
+      const double v = std::exp(m * lam);
+      g.e[m + 2].hi = (float)v;
+      g.e[m + 2].lo = (float)(v - (double)(float)v);
+    }
+    if (tc) {
+      if (!tc_prepare_const(dC64, N, const_is_a ? 0 : 1, dSl, dExp, tmap, 0)) {
+        st = NMC_ECUDA;
+      } else {
+        g.oz_const = dSl;
+        g.oz_const_exp = dExp;
+        gemm_tc(g, const_is_a != 0, tmap, dErr, 0);
+      }
+    } else {
+      gemm_df(g, 0);
+    }
+    int err = 0;
+    if (st == NMC_OK) {
+      if (cudaDeviceSynchronize() != cudaSuccess ||
+          cudaMemcpy(&err, dErr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(C, dOut, mats * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        st = NMC_ECUDA;
+      } else if (err) {
+        st = NMC_ETIMEOUT;
+      }
+    }
+  }
+  for (void* p : bufs) cudaFree(p);
+  return st;
+}
 
 nmc_status nmc_graph_stats(const nmc_ctx* x, long long* recorded, long long* replayed) {
   if (!x) return NMC_EINVAL;

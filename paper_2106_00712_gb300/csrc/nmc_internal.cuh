@@ -115,18 +115,26 @@ struct DfGemmArgs {
   long long fstride = 0;
   int ns = 2;  // spins per chain in the batch
   df2 e[5];    // e^{m lam}, m = -2..2
-  // tensor-core path: integer BF16 slices of the constant operand and their scale
-  // exponents (row exponents when it is A, column exponents when it is B)
+  // tensor-core path: BF16 slices of the constant operand and the exponents of its rows
+  // (constant on the left) or columns (constant on the right)
   const void* oz_const = nullptr;
   const int* oz_const_exp = nullptr;
 };
 void gemm_df(const DfGemmArgs& g, cudaStream_t st);
-// Same product on the BF16 tensor cores by exact integer slicing (N <= 64); the constant
-// operand (A if const_is_a, else B) is given by oz_const / oz_const_exp.
-void gemm_oz(const DfGemmArgs& g, bool const_is_a, cudaStream_t st);
-bool gemm_oz_supported(int N);
-size_t oz_const_elems();  // bf16 elements of one sliced constant
-void slice_const(const double* M, int N, int as_b, void* out, int* exps, cudaStream_t st);
+// The same products on the tcgen05 tensor cores (accumulators in tensor memory, the constant's
+// slices copied by TMA), any N <= 320. Geometry of the tiling for a given N:
+struct TcShape { int N, NT, KC, KP, n_chunks, n_tiles; };
+TcShape tc_shape(int N);
+bool gemm_tc_supported(int N);
+size_t tc_const_elems(int N);   // bf16 elements of one sliced constant (one orientation)
+// Slice the constant M (as_b = 0: C = M X, rows of M; as_b = 1: C = X M, columns of M) into
+// `slices` (device, tc_const_elems(N) bf16), its exponents into `exps` (device, N ints), and
+// encode the TMA tensor map over the slices into `tmap` (host, 128 bytes, 64-aligned).
+// Returns false if the tensor map cannot be encoded.
+bool tc_prepare_const(const double* M, int N, int as_b, void* slices, int* exps, void* tmap,
+                      cudaStream_t st);
+// g.oz_const_exp = the constant's exponents; err: device int, set on a bounded-wait expiry.
+void gemm_tc(const DfGemmArgs& g, bool const_is_a, const void* tmap, int* err, cudaStream_t st);
 void split_to_df(const double* x, df2* y, long long n, cudaStream_t st);
 
 // ---------------------------------------------------------------------------- UDT

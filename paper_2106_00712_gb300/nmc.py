@@ -27,7 +27,7 @@ EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_field
             "nmc_measure", "nmc_get_fields", "nmc_get_green", "nmc_get_dims",
             "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_series", "nmc_philox", "nmc_philox_device",
             "nmc_drift_history", "nmc_profile", "nmc_kernel_stats", "nmc_graph_stats",
-            "nmc_green_noalloc", "nmc_debug_fail_alloc", "nmc_fma_probe",
+            "nmc_green_noalloc", "nmc_debug_fail_alloc", "nmc_fma_probe", "nmc_debug_product",
             "nmc_last_error",
             "nmc_version", "nmc_destroy")
 
@@ -126,6 +126,7 @@ def load():
         "nmc_green_noalloc": (i, [i, i, i, d, vp, vp, i, vp, vp]),
         "nmc_debug_fail_alloc": (None, [ctypes.c_longlong]),
         "nmc_fma_probe": (i, [i, i, i, i, vp, vp]),
+        "nmc_debug_product": (i, [i, i, i, i, vp, vp, vp, i, i, i, i, d, vp, vp]),
         "nmc_last_error": (ctypes.c_char_p, [vp]),
         "nmc_version": (ctypes.c_char_p, []),
         "nmc_destroy": (None, [vp]),
@@ -367,6 +368,25 @@ def nmc_fma_probe(kind, blocks, threads, iters, d_out_ptr, stream=None):
         raise NmcError(st, "nmc_fma_probe")
 
 
+def nmc_debug_product(precision, cst, X, const_is_a, fields=None, br=0, bc=0, cr=0, cc=0,
+                      lam=0.0, colscale=None):
+    """One batched product of the compensated modes on host arrays (testing hook):
+    C[b] = cst @ X[b] (const_is_a) or X[b] @ cst, with the optional field and column
+    scalings of include/nmc.h. Returns C as float64 [batch][N][N]."""
+    cst = np.ascontiguousarray(cst, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    batch, N, _ = X.shape
+    C = np.empty_like(X)
+    f = None if fields is None else np.ascontiguousarray(fields, dtype=np.int8)
+    cs = None if colscale is None else np.ascontiguousarray(colscale, dtype=np.float64)
+    st = load().nmc_debug_product(int(precision), N, batch, int(bool(const_is_a)), _ptr(cst),
+                                  _ptr(X), None if f is None else _ptr(f), br, bc, cr, cc,
+                                  float(lam), None if cs is None else _ptr(cs), _ptr(C))
+    if st != NMC_OK:
+        raise NmcError(st, "nmc_debug_product")
+    return C
+
+
 def nmc_destroy(ctx):
     load().nmc_destroy(ctx)
 
@@ -393,7 +413,8 @@ class Context:
         try:
             nmc_configure(self.ctx, o)
         except Exception:
-            nmc_destroy(self.ctx)
+            ctx, self.ctx = self.ctx, None
+            nmc_destroy(ctx)
             raise
 
     def __enter__(self):
