@@ -42,11 +42,12 @@ namespace nmc {
 
 namespace {
 
-constexpr int kS = 6;            // slices per operand
+constexpr int kS = 7;            // slices per operand
 constexpr int kLoFirst = 3;      // first slice of the lo part of an FP32 pair
-constexpr int kAcc = 4;          // accumulators: groups 0, 1, 2 exact, 3..5 merged
+constexpr int kAcc = kS;         // one accumulator per group g = s + t = 0..6
 constexpr int kM = 128;          // tile rows = tensor-memory lanes
-constexpr int kThreads = 128;
+constexpr int kSlicers = 512;    // 16 warps: slicing and epilogue
+constexpr int kThreads = kSlicers + 32;   // + one warp issuing the TMA copies and the MMAs
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz: a bounded wait
 constexpr int kMaxTcN = 320;     // exactness of the group-2 sums needs K <= 340
 
@@ -64,6 +65,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -161,6 +166,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// exact sum of two floats as a normalized pair (Knuth's TwoSum)
+__device__ __forceinline__ df2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df2{s, e};
+}
+
+// pair + float: TwoSum of the high parts, the low part added, then renormalized
+__device__ __forceinline__ df2 df_add_f(df2 a, float x) {
+  const df2 t = two_sum(a.hi, x);
+  return df_norm(t.hi, __fadd_rn(t.lo, a.lo));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -176,35 +206,32 @@ __device__ __forceinline__ float round_to_slice(float r, int s) {
 }
 
 // Cut 8 values (FP32 pairs already scaled into (-1/2, 1/2)) into kS pre-scaled slices and
-// pack each slice's 8 values as BF16 (exact: integers <= 256 times a power of two).
-__device__ __forceinline__ void slice8(const df2 (&v)[8], uint4 (&out)[kS]) {
-  float c[kS][8];
+// store each slice's 8 values as BF16 (exact: integers <= 256 times a power of two), 16
+// bytes per slice at dst + s * stride.
+__device__ __forceinline__ void slice8_store(const df2 (&v)[8], uint8_t* dst, int stride) {
+  float r[8], q[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    float r = v[j].hi;
-#pragma unroll
-    for (int s = 0; s < kS; ++s) {
-      const float cs = round_to_slice(r, s);
-      r = __fsub_rn(r, cs);   // exact
-      c[s][j] = cs;
-    }
-    float q = v[j].lo;        // |lo| < 2^-25: its first slice is s = 3
-#pragma unroll
-    for (int s = kLoFirst; s < kS; ++s) {
-      const float cs = round_to_slice(q, s);
-      q = __fsub_rn(q, cs);
-      c[s][j] = __fadd_rn(c[s][j], cs);   // exact: both multiples of q_s, sum <= 256 q_s
-    }
-  }
+  for (int j = 0; j < 8; ++j) r[j] = v[j].hi, q[j] = v[j].lo;
 #pragma unroll
   for (int s = 0; s < kS; ++s) {
+    float c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      c[j] = round_to_slice(r[j], s);
+      r[j] = __fsub_rn(r[j], c[j]);   // exact
+      if (s >= kLoFirst) {            // |lo| < 2^-25: its first slice is s = 3
+        const float cl = round_to_slice(q[j], s);
+        q[j] = __fsub_rn(q[j], cl);
+        c[j] = __fadd_rn(c[j], cl);   // exact: both multiples of q_s, sum <= 256 q_s
+      }
+    }
+    // every slice is exact in BF16, so its BF16 pattern is the upper half of its FP32 one:
+    // pack two with one byte permutation (low half = the even element)
     uint32_t w[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const __nv_bfloat162 b = __floats2bfloat162_rn(c[s][2 * h], c[s][2 * h + 1]);
-      w[h] = *reinterpret_cast<const uint32_t*>(&b);
-    }
-    out[s] = make_uint4(w[0], w[1], w[2], w[3]);
+    for (int h = 0; h < 4; ++h)
+      w[h] = __byte_perm(__float_as_uint(c[2 * h]), __float_as_uint(c[2 * h + 1]), 0x7632);
+    *reinterpret_cast<uint4*>(dst + s * stride) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -226,29 +253,48 @@ struct TcGeom {
   int* err;           // device error flag (bounded waits)
 };
 
-// Shared-memory layout (bytes, from a 1024-aligned base): A slices [kS][kM/8][KC/8][8][8] bf16,
-// then B slices [kS][NT/8][KC/8][8][8] bf16, then barriers and per-row/column exponents.
+// Shared memory (bytes, from a 1024-aligned base): two stages of A slices
+// [kS][kM/8][KC/8][8][8] bf16, then two stages of B slices [kS][NT/8][KC/8][8][8] bf16.
 __host__ __device__ inline int a_bytes(int KC) { return kS * kM * KC * 2; }
 __host__ __device__ inline int b_bytes(int NT, int KC) { return kS * NT * KC * 2; }
+__host__ __device__ inline uint32_t tmem_columns(int cols) {
+  return cols <= 64 ? 64u : cols <= 128 ? 128u : cols <= 256 ? 256u : 512u;
+}
 
+constexpr int kKParts = kSlicers / kM;   // slicing threads per row of the tile (4)
+constexpr int kCache = 2;                // chunks of a row kept in registers (N <= 64)
+
+// One (row tile, column tile) of D = A B^T. Slicing thread t (< 512) handles row
+// r = t % 128 of the tile and, in every K chunk, the 8-wide K group t / 128 (of KC / 8): it
+// scans, field-scales and slices those entries into the chunk's stage, then its warp signals
+// the stage full. The last warp issues the TMA copies of the constant's slices and the MMAs
+// of each full stage, and releases the stage when they complete. In the epilogue slicing
+// warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its permitted quarter) and 16
+// columns starting at 16 (w / 4).
 template <bool CONST_A>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const DfGemmArgs g, const TcGeom geo, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ uint8_t smraw[];
-  __shared__ uint64_t bar_tma, bar_mma;
+  __shared__ uint64_t bar_tma[2], bar_mma[2], bar_full[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int fexp[64];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int N = g.N, NT = geo.NT, KC = geo.KC;
+  __shared__ int rexp[kM];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = g.N, NT = geo.NT, KC = geo.KC, n_chunks = geo.n_chunks;
   const int n_tile = blockIdx.y;
+  const bool mma_warp = warp == kSlicers / 32;
   uint8_t* base = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  uint8_t* As = base;
-  uint8_t* Bs = base + a_bytes(KC);
-  const uint32_t tmem_cols = (uint32_t)(kAcc * NT <= 64 ? 64 : kAcc * NT <= 128 ? 128 : 256);
+  // stage st: A slices at base + st * a_bytes, B slices at base + 2 a_bytes + st * b_bytes
+  auto As = [&](int st) { return base + st * a_bytes(KC); };
+  auto Bs = [&](int st) { return base + 2 * a_bytes(KC) + st * b_bytes(NT, KC); };
+  const uint32_t tmem_cols = tmem_columns(kAcc * NT);
 
   if (tid == 0) {
-    mbar_init(&bar_tma, 1);
-    mbar_init(&bar_mma, 1);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&bar_tma[k], 1);
+      mbar_init(&bar_mma[k], 1);
+      mbar_init(&bar_full[k], kSlicers / 32);   // one arrival per slicing warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_proxy_async();
   }
@@ -263,14 +309,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int n = n_tile * NT + tid;
     fexp[tid] = n < N ? g.oz_const_exp[n] : 0;
   }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_base_sh;
 
   // this thread's row of the chain operand: matrix b, index i (a row of X, or a column of X
-  // when the constant is on the left)
-  const long long grow = (long long)blockIdx.x * kM + tid;
+  // when the constant is on the left), and its K group within each chunk
+  // four consecutive lanes share a row (one K group each), so a warp reads eight rows'
+  // 256-byte runs and writes eight rows' 16-byte slice pieces into 512 contiguous bytes
+  const int r = (warp * 8 + (lane >> 2)) & (kM - 1), kp = lane & (kKParts - 1);
+  const bool kpart = !mma_warp && kp * 8 < KC;   // KC = 16: only two K groups per chunk
+  const long long grow = (long long)blockIdx.x * kM + r;
   const bool valid = grow < geo.rows;
   const int b = valid ? (int)(grow / N) : 0;
   const int i = valid ? (int)(grow % N) : 0;
@@ -279,127 +325,188 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int sg = (g.ns == 2 && (b & 1)) ? -1 : 1;
   const long long fchain = (long long)(g.ns == 2 ? b >> 1 : b) * g.fstride;
   const bool bf = g.bfields != nullptr;
-  const int si_b = bf ? field_sign(g.bfields, fchain + i) : 1;
-  // element k of the row: X[k][i] (constant on the left) or X[i][k]
-  auto elem = [&](int k) -> df2 { return CONST_A ? X[(long long)k * ldx + i] : X[(long long)i * ldx + k]; };
-  auto fmul = [&](int k) -> int {   // field multiple m in e^{m lam} of element k
-    if (!bf) return 0;
-    const int sk = field_sign(g.bfields, fchain + k);
-    // X's (row, col) = (k, i) or (i, k)
-    return CONST_A ? sg * (g.br * sk + g.bc * si_b) : sg * (g.br * si_b + g.bc * sk);
-  };
-
-  // pass 1: row maximum after the field scaling -> exponent
-  int xexp = 0;
-  if (valid) {
-    float mx = 0.f;
-    for (int k = 0; k < N; ++k) {
-      const df2 v = elem(k);
-      const int m = fmul(k);
-      mx = fmaxf(mx, fabsf(v.hi) * (m ? g.e[m + 2].hi : 1.f));
+  const int si_b = bf && valid ? field_sign(g.bfields, fchain + i) : 1;
+  // 8 entries k0 .. k0 + 7 of the row (X[k][i] or X[i][k]) with their field factors: the
+  // loads are issued together, then scaled
+  auto load8 = [&](int k0, df2 (&v)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = k0 + j;
+      v[j] = (valid && k < N) ? (CONST_A ? X[(long long)k * ldx + i] : X[(long long)i * ldx + k])
+                              : df_zero();
     }
-    xexp = row_exponent(mx);
-  }
-  const float xs = p2(-xexp);
-  const uint32_t idesc = idesc_bf16(kM, NT);
-  const uint32_t lbo = 128, sbo = (uint32_t)(KC / 8) * 128;
-  const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
-  const int box_rows = kS * (NT / 8) * (KC / 8);
-  bool ok = true;
-
-  for (int kc = 0; kc < geo.n_chunks; ++kc) {
-    if (kc > 0) ok = mbar_wait(&bar_mma, (kc - 1) & 1, geo.err, 1) && ok;   // stage free
-    if (tid == 0 && ok) {
-      mbar_expect_tx(&bar_tma, (uint32_t)b_bytes(NT, KC));
-      tma_load_2d(Bs, &tmap, 0, (n_tile * geo.n_chunks + kc) * box_rows, &bar_tma);
-    }
-    // slice this thread's row, K range [kc KC, kc KC + KC), 8 at a time
-    for (int kg = 0; kg < KC / 8; ++kg) {
-      df2 v[8];
+    if (bf) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int k = kc * KC + kg * 8 + j;
-        df2 x = df_zero();
-        if (valid && k < N) {
-          x = elem(k);
-          const int m = fmul(k);
-          if (m) x = df_mul(x, g.e[m + 2]);
-          x.hi *= xs;
-          x.lo *= xs;
-        }
-        v[j] = x;
+        const int k = k0 + j;
+        if (!valid || k >= N) continue;
+        const int sk = field_sign(g.bfields, fchain + k);
+        const int m = CONST_A ? sg * (g.br * sk + g.bc * si_b) : sg * (g.br * si_b + g.bc * sk);
+        if (m) v[j] = df_mul(v[j], g.e[m + 2]);
       }
-      uint4 sl[kS];
-      slice8(v, sl);
-      uint8_t* dst = As + (tid >> 3) * (KC / 8) * 128 + kg * 128 + (tid & 7) * 16;
-#pragma unroll
-      for (int s = 0; s < kS; ++s) *reinterpret_cast<uint4*>(dst + s * (kM * KC * 2)) = sl[s];
     }
-    fence_proxy_async();   // the slices, written by threads, are read by the tensor core
-    __syncthreads();
-    if (tid == 0 && ok) {
-      ok = mbar_wait(&bar_tma, kc & 1, geo.err, 2);
-      tc_fence_after();
-      if (ok) {
+  };
+
+  // pass 1: this thread's share of the row maximum (its entries kept when N <= 64)
+  const bool cache = n_chunks <= kCache;
+  df2 keep[kCache][8];
+  float mx = 0.f;
+  if (kpart) {
+    if (cache) {
+      load8(kp * 8, keep[0]);
+      if (n_chunks > 1) load8(KC + kp * 8, keep[1]);
+#pragma unroll
+      for (int c = 0; c < kCache; ++c)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mx = fmaxf(mx, (c < n_chunks) ? fabsf(keep[c][j].hi) : 0.f);
+    } else {
+      for (int c = 0; c < n_chunks; ++c) {
+        df2 v[8];
+        load8(c * KC + kp * 8, v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mx = fmaxf(mx, fabsf(v[j].hi));
+      }
+    }
+  }
+  // the row maximum over the row's four lanes
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  if (!mma_warp && kp == 0) rexp[r] = row_exponent(mx);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  bool ok = true;
+
+  if (mma_warp) {
+    // ---------------------------------------------------------------- TMA + MMA warp
+    if (lane == 0) {
+      const uint32_t lbo = 128, sbo = (uint32_t)(KC / 8) * 128;
+      const int box_rows = kS * (NT / 8) * (KC / 8);
+      // the constant's first two chunks: both stages are free
+      for (int c = 0; c < 2 && c < n_chunks; ++c) {
+        mbar_expect_tx(&bar_tma[c], (uint32_t)b_bytes(NT, KC));
+        tma_load_2d(Bs(c), &tmap, 0, (n_tile * n_chunks + c) * box_rows, &bar_tma[c]);
+      }
+      for (int kc = 0; kc < n_chunks && ok; ++kc) {
+        const int st = kc & 1, use = kc >> 1;
+        ok = mbar_wait(&bar_full[st], use & 1, geo.err, 3) && ok;   // A slices written
+        ok = mbar_wait(&bar_tma[st], use & 1, geo.err, 4) && ok;    // B slices landed
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(As(st)), b_base = smem_u32(Bs(st));
+        // One instruction multiplies A slice s by up to four consecutive B slices t0..t0+3,
+        // stacked along N: its D columns (s + t) NT are exactly group s + t's accumulator.
         for (int ks = 0; ks < KC / 16; ++ks) {
 #pragma unroll 1
           for (int s = 0; s < kS; ++s) {
             const uint64_t ad = smem_desc(a_base + s * (kM * KC * 2) + ks * 256, lbo, sbo);
-            for (int t = 0; s + t < kS; ++t) {
-              const int grp = s + t < 3 ? s + t : 3;
-              const uint64_t bd = smem_desc(b_base + t * (NT * KC * 2) + ks * 256, lbo, sbo);
-              // the first product into each accumulator overwrites it
-              const bool first = kc == 0 && ks == 0 && (grp < 3 ? s == 0 : (s == 0 && t == 3));
-              mma_bf16_ss(tmem + (uint32_t)(grp * NT), ad, bd, idesc, first ? 0u : 1u);
+            for (int t0 = 0; s + t0 < kS; t0 += 4) {
+              const int m = kS - s - t0 < 4 ? kS - s - t0 : 4;
+              const uint64_t bd = smem_desc(b_base + t0 * (NT * KC * 2) + ks * 256, lbo, sbo);
+              // the first instructions (s = 0) write every accumulator once: overwrite
+              const bool first = kc == 0 && ks == 0 && s == 0;
+              mma_bf16_ss(tmem + (uint32_t)((s + t0) * NT), ad, bd, idesc_bf16(kM, m * NT),
+                          first ? 0u : 1u);
             }
           }
         }
+        mma_commit(&bar_mma[st]);   // arrives when this chunk's MMAs have completed
+        // with this chunk's MMAs queued, wait for the previous chunk's and refill its stage
+        // with the constant's chunk kc + 1
+        if (kc >= 1 && kc + 1 < n_chunks) {
+          const int pst = (kc - 1) & 1;
+          ok = mbar_wait(&bar_mma[pst], ((kc - 1) >> 1) & 1, geo.err, 2) && ok;
+          if (!ok) break;
+          mbar_expect_tx(&bar_tma[pst], (uint32_t)b_bytes(NT, KC));
+          tma_load_2d(Bs(pst), &tmap, 0, (n_tile * n_chunks + kc + 1) * box_rows, &bar_tma[pst]);
+        }
       }
-      mma_commit(&bar_mma);   // arrives when the MMAs above have completed
     }
-    __syncthreads();
-  }
-  ok = mbar_wait(&bar_mma, (geo.n_chunks - 1) & 1, geo.err, 3) && ok;
-  tc_fence_after();
-
-  // epilogue: this thread's lane of the four accumulators, 16 columns at a time
-  const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-  const bool cf = g.cfields != nullptr;
-  const int si_c = cf ? field_sign(g.cfields, fchain + i) : 1;
-  for (int c0 = 0; c0 < NT; c0 += 16) {
-    float acc[kAcc][16];
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- slicing warps
+    const float xs = p2(-rexp[r]);
+    for (int kc = 0; kc < n_chunks; ++kc) {
+      const int st = kc & 1, use = kc >> 1;
+      if (kc >= 2)   // this stage's previous MMAs (chunk kc - 2) have completed
+        ok = mbar_wait(&bar_mma[st], (use - 1) & 1, geo.err, 1) && ok;
+      if (kpart) {
+        df2 v[8];
+        if (cache) {
 #pragma unroll
-    for (int q = 0; q < kAcc; ++q) tmem_ld16(lane_addr + (uint32_t)(q * NT + c0), acc[q]);
-    tmem_wait_ld();
-    if (!valid || !ok) continue;
+          for (int j = 0; j < 8; ++j) v[j] = kc == 0 ? keep[0][j] : keep[1][j];
+        } else {
+          load8(kc * KC + kp * 8, v);
+        }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int n = n_tile * NT + c0 + j;
-      if (n >= N) continue;
-      // groups 0 and 1 as an exact pair, then add groups 2 and 3..6
-      const float s01 = __fadd_rn(acc[0][j], acc[1][j]);
-      const float bb = __fsub_rn(s01, acc[0][j]);
-      const float e01 = __fadd_rn(__fsub_rn(acc[0][j], __fsub_rn(s01, bb)), __fsub_rn(acc[1][j], bb));
-      df2 sum = df_norm(s01, e01);
-      sum = df_add(sum, df2{acc[2][j], 0.f});
-      sum = df_add(sum, df2{acc[3][j], 0.f});
-      const int ex = xexp + fexp[c0 + j];
-      const float se = (ex >= -126 && ex <= 127) ? p2(ex) : ldexpf(1.f, ex);
-      df2 out{sum.hi * se, sum.lo * se};
-      // output element C[r][c]: (n, i) when the constant is on the left, else (i, n)
-      const int r = CONST_A ? n : i, c = CONST_A ? i : n;
-      if (cf) {
-        const int sn = field_sign(g.cfields, fchain + n);
-        const int m = CONST_A ? sg * (g.cr * sn + g.cc * si_c) : sg * (g.cr * si_c + g.cc * sn);
-        if (m) out = df_mul(out, g.e[m + 2]);
+        for (int j = 0; j < 8; ++j) v[j] = df2{v[j].hi * xs, v[j].lo * xs};
+        slice8_store(v, As(st) + (r >> 3) * (KC / 8) * 128 + kp * 128 + (r & 7) * 16,
+                     kM * KC * 2);
       }
-      const long long idx = (long long)b * g.sC + (long long)r * g.ldc + c;
-      if (g.Cd) {
-        double d = df_to_double(out);
-        if (g.colscale) d *= g.colscale[(long long)b * g.sColscale + c];
-        g.Cd[idx] = d;
-      } else {
-        g.C[idx] = out;
+      fence_proxy_async();   // the slices, written by threads, are read by the tensor core
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_full[st]);
+    }
+    {
+      const int last = n_chunks - 1;
+      ok = mbar_wait(&bar_mma[last & 1], (last >> 1) & 1, geo.err, 5) && ok;
+    }
+    tc_fence_after();
+
+    // ------------------------------------------------------------ epilogue (slicing warps)
+    const int lq = warp & 3, cq = warp >> 2;
+    const int c0 = cq * 16;
+    if (c0 < NT) {
+      const int re = lq * 32 + lane;   // the tile row of this lane
+      const long long grow_e = (long long)blockIdx.x * kM + re;
+      const bool valid_e = grow_e < geo.rows;
+      const int be = valid_e ? (int)(grow_e / N) : 0;
+      const int ie = valid_e ? (int)(grow_e % N) : 0;
+      const int sge = (g.ns == 2 && (be & 1)) ? -1 : 1;
+      const long long fch = (long long)(g.ns == 2 ? be >> 1 : be) * g.fstride;
+      const uint32_t lane_addr = tmem + ((uint32_t)(lq * 32) << 16);
+      const int xe = rexp[re];
+      const bool cf = g.cfields != nullptr;
+      const int si_c = cf && valid_e ? field_sign(g.cfields, fch + ie) : 1;
+      for (int h = 0; h < 16; h += 8) {
+        // groups 0 and 1 as exact pairs, then the other accumulators added in FP32 pairs
+        float a[kAcc][8];
+#pragma unroll
+        for (int q = 0; q < kAcc; ++q) tmem_ld8(lane_addr + (uint32_t)(q * NT + c0 + h), a[q]);
+        tmem_wait_ld();
+        if (!valid_e || !ok) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int n = n_tile * NT + c0 + h + j;
+          if (n >= N) continue;
+          // groups 4..6 (below 2^-32 of the product) summed in FP32, smallest first; groups
+          // 0 and 1 as an exact pair, then groups 2, 3 and that sum added in FP32 pairs
+          const float t = __fadd_rn(__fadd_rn(a[6][j], a[5][j]), a[4][j]);
+          df2 sum = two_sum(a[0][j], a[1][j]);
+          sum = df_add_f(sum, a[2][j]);
+          sum = df_add_f(sum, a[3][j]);
+          sum = df_add_f(sum, t);
+          const int ex = xe + fexp[c0 + h + j];
+          const float se = (ex >= -126 && ex <= 127) ? p2(ex) : ldexpf(1.f, ex);
+          df2 out{sum.hi * se, sum.lo * se};
+          // output element C[rr][cc]: (n, i) when the constant is on the left, else (i, n)
+          const int rr = CONST_A ? n : ie, cc = CONST_A ? ie : n;
+          if (cf) {
+            const int sn = field_sign(g.cfields, fch + n);
+            const int m =
+                CONST_A ? sge * (g.cr * sn + g.cc * si_c) : sge * (g.cr * si_c + g.cc * sn);
+            if (m) out = df_mul(out, g.e[m + 2]);
+          }
+          const long long idx = (long long)be * g.sC + (long long)rr * g.ldc + cc;
+          if (g.Cd) {
+            double d = df_to_double(out);
+            if (g.colscale) d *= g.colscale[(long long)be * g.sColscale + cc];
+            g.Cd[idx] = d;
+          } else {
+            g.C[idx] = out;
+          }
+        }
       }
     }
   }
@@ -437,15 +544,11 @@ __global__ void k_tc_slice_const(const double* M, int N, int as_b, int NT, int K
       df2 x = df_from_double(elem(k0 + j));
       v[j] = df2{x.hi * fs, x.lo * fs};
     }
-    uint4 sl[kS];
-    slice8(v, sl);
     const int kc = k0 / KC, kg = (k0 % KC) / 8;
     const long long blk = (long long)nt * n_chunks + kc;
     const long long off = blk * kS * NT * KC + (long long)(nn >> 3) * (KC / 8) * 64 + kg * 64 +
                           (nn & 7) * 8;
-#pragma unroll
-    for (int s = 0; s < kS; ++s)
-      *reinterpret_cast<uint4*>(out + off + (long long)s * NT * KC) = sl[s];
+    slice8_store(v, (uint8_t*)(out + off), NT * KC * 2);
   }
 }
 
@@ -524,9 +627,9 @@ void gemm_tc(const DfGemmArgs& g, bool const_is_a, const void* tmap, int* err,
   TcGeom geo{s.NT, s.KC, s.KP, s.n_chunks, s.n_tiles, (long long)g.batch * g.N, err};
   // Tensor memory holds 512 columns per SM: request enough shared memory that no more CTAs
   // share an SM than their accumulators fit (228 KB per SM, 1 KB reserved per CTA).
-  const int cols = kAcc * s.NT <= 64 ? 64 : kAcc * s.NT <= 128 ? 128 : 256;
+  const int cols = (int)tmem_columns(kAcc * s.NT);
   const size_t fit = 233472 / (512 / cols + 1) - 1024 + 16;
-  size_t smem = (size_t)a_bytes(s.KC) + b_bytes(s.NT, s.KC) + 1024;
+  size_t smem = (size_t)2 * (a_bytes(s.KC) + b_bytes(s.NT, s.KC)) + 1024;
   if (smem < fit) smem = fit;
   const dim3 grid((unsigned)((geo.rows + kM - 1) / kM), (unsigned)s.n_tiles);
   const CUtensorMap& m = *(const CUtensorMap*)tmap;
