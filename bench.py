@@ -43,9 +43,9 @@ NOMINAL_TFLOPS = {"fp64": 1.259, "fp32": 80.55}
 # Compensated FP32 pairs: one multiply-add costs 12 FP32-pipe instructions (TwoProd by FMA,
 # TwoSum, two cross-term FMAs, two adds); a secondary ceiling for the pair kernels.
 PAIR_INSTR_PER_FMA = 12
-# exact-slicing tensor-core products: 6 BF16 slices per operand, the 21 slice pairs (s, t)
-# with s + t <= 5 issued per FP64-class product
-OZ_PRODUCTS = 21
+# exact-slicing tensor-core products: 7 BF16 slices per operand, the 28 slice pairs (s, t)
+# with s + t <= 6 issued per FP64-class product
+OZ_PRODUCTS = 28
 TC_KERNEL = "k_gemm_tc (tcgen05.mma kind::f16, TMEM accumulators, TMA-staged constant slices)"
 
 
