@@ -5,8 +5,8 @@
 //   column of largest norm (lowest index on ties) is swapped into place, a reflector
 //   H_p = I - tau v v^T (v_p = 1) zeroes it below the diagonal, and the trailing columns
 //   are updated; squared column norms are downdated with the usual safeguard (recomputed
-//   when the downdated value has lost more than half its digits). Outputs U = Q (formed by
-//   backward accumulation of the reflectors), D = |diag R| and T = D^{-1} R P^T.
+//   when the downdated value has lost more than half its digits). Outputs U = Q (formed in
+//   place by backward accumulation of the reflectors), D = |diag R| and T = D^{-1} R P^T.
 // k_solve: Y = X^{-1} (Db_R^{-1} U_R^T) by Gauss-Jordan elimination with partial pivoting
 //   on the augmented matrix [X | RHS]; X is the well-scaled middle factor of the
 //   stabilized inverse, so partial pivoting is sufficient.
@@ -69,16 +69,11 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   double* n2 = n1 + N;
   double* tau = n2 + N;
   int* perm = (int*)(tau + N);
-  __shared__ int s_piv;
-  double* W;  // column-major: W[c*N + r]
-  double* Q;  // column-major
-  if (use_smem) {
+  double* W;  // column-major: W[c*N + r]; becomes Q at the end
+  if (use_smem)
     W = (double*)(smraw + ((qrp_small_bytes(N) + 15) & ~(size_t)15));
-    Q = W + NN;
-  } else {
+  else
     W = ws + (long long)b * 2 * NN;
-    Q = W + NN;
-  }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int sub = tid & (kQuad - 1);
   const unsigned qmask = 0xFu << (lane & ~(kQuad - 1));
@@ -103,30 +98,28 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
 
   const double tol3z = sqrt(DBL_EPSILON);
   for (int p = 0; p < N; ++p) {
+    // warp 0: pivot (largest remaining norm, lowest index on ties), swap, reflector
+    // H_p = I - tau v v^T (v_p = 1) zeroing W[p+1:, p]; the other warps wait at the barrier
     if (warp == 0) {
       double best = -1.0;
       int bi = N;
       for (int c = p + lane; c < N; c += 32)
         if (n1[c] > best) { best = n1[c]; bi = c; }
       warp_argmax(best, bi);
-      if (lane == 0) s_piv = bi;
-    }
-    __syncthreads();
-    const int piv = s_piv;
-    if (piv != p) {
-      for (int r = tid; r < N; r += kThreads) {
-        const double t0 = W[(long long)p * N + r];
-        W[(long long)p * N + r] = W[(long long)piv * N + r];
-        W[(long long)piv * N + r] = t0;
+      const int piv = bi;
+      if (piv != p) {
+        for (int r = lane; r < N; r += 32) {
+          const double t0 = W[(long long)p * N + r];
+          W[(long long)p * N + r] = W[(long long)piv * N + r];
+          W[(long long)piv * N + r] = t0;
+        }
+        if (lane == 0) {
+          double t1 = n1[p]; n1[p] = n1[piv]; n1[piv] = t1;
+          t1 = n2[p]; n2[p] = n2[piv]; n2[piv] = t1;
+          const int ti = perm[p]; perm[p] = perm[piv]; perm[piv] = ti;
+        }
       }
-      if (tid == 0) {
-        double t1 = n1[p]; n1[p] = n1[piv]; n1[piv] = t1;
-        t1 = n2[p]; n2[p] = n2[piv]; n2[piv] = t1;
-        const int ti = perm[p]; perm[p] = perm[piv]; perm[piv] = ti;
-      }
-    }
-    __syncthreads();
-    if (warp == 0) {  // reflector H_p = I - tau v v^T, v_p = 1, zeroing W[p+1:, p]
+      __syncwarp();
       double* col = W + (long long)p * N;
       const double alpha = col[p];
       double xn2 = 0.0;
@@ -187,32 +180,34 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
     const double d = fabs(W[r * N + r]);
     Tb[r * N + perm[c]] = (c >= r) ? W[c * N + r] / d : 0.0;
   }
-  // Q = H_0 H_1 ... H_{N-1} by backward accumulation (column-major)
-  for (int e = tid; e < (int)NN; e += kThreads) {
-    const int c = e / N, r = e - c * N;
-    Q[e] = (r == c) ? 1.0 : 0.0;
-  }
-  __syncthreads();
+  __syncthreads();   // T and D are out: W's upper triangle is free
+  // Q = H_0 H_1 ... H_{N-1} in place over W (column-major), by backward accumulation:
+  // before step p, columns > p hold H_{p+1} ... H_{N-1} in rows > p (rows <= p still hold R
+  // and are treated as zero); step p applies H_p to those columns, writing their row p, and
+  // then turns column p (the reflector v, v_p = 1) into H_p e_p.
   for (int p = N - 1; p >= 0; --p) {
     const double tp = tau[p];
-    if (tp != 0.0) {
-      const double* v = W + (long long)p * N;
-      for (int c0 = p; c0 < N; c0 += kColsPerPass) {
-        const int c = c0 + tid / kQuad;
-        if (c < N) {
-          double* col = Q + (long long)c * N;
-          double dot = 0.0;
-          for (int r = p + 1 + sub; r < N; r += kQuad) dot += v[r] * col[r];
-          dot = quad_sum(dot, qmask) + col[p];
-          const double f = tp * dot;
+    const double* v = W + (long long)p * N;
+    for (int c0 = p + 1; c0 < N; c0 += kColsPerPass) {
+      const int c = c0 + tid / kQuad;
+      if (c < N) {
+        double* col = W + (long long)c * N;
+        double dot = 0.0;
+        for (int r = p + 1 + sub; r < N; r += kQuad) dot += v[r] * col[r];
+        const double f = tp * quad_sum(dot, qmask);
+        if (f != 0.0)
           for (int r = p + 1 + sub; r < N; r += kQuad) col[r] -= f * v[r];
-          __syncwarp(qmask);
-          if (sub == 0) col[p] -= f;
-        }
+        __syncwarp(qmask);
+        if (sub == 0) col[p] = -f;
       }
     }
     __syncthreads();
+    double* cp = W + (long long)p * N;
+    for (int r = tid; r < N; r += kThreads)
+      cp[r] = r < p ? 0.0 : r == p ? 1.0 - tp : -tp * cp[r];
+    __syncthreads();
   }
+  double* Q = W;
   double* Ub = U + (long long)b * NN;
   for (int e = tid; e < (int)NN; e += kThreads) {
     const int r = e / N, c = e - r * N;
@@ -286,7 +281,7 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
 void qrp_udt(const double* X, double* U, double* D, double* Tp, double* ws, int N, int batch,
              cudaStream_t st) {
   const size_t small = (qrp_small_bytes(N) + 15) & ~(size_t)15;
-  const size_t big = small + 2 * (size_t)N * N * sizeof(double);
+  const size_t big = small + (size_t)N * N * sizeof(double);
   const int use_smem = big <= kSmemLimit;
   const size_t bytes = use_smem ? big : small;
   allow_max_dynamic_smem((const void*)k_qrp);
