@@ -63,6 +63,14 @@ BF16_PEAK, BF16_PEAK_SUSTAINED = _measured_peaks_file()
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel source at
 # capture time; reported as null once the source has changed.
 TRAFFIC = {
+    # k_gemm_tc, bench launch configuration (512 products of 64 x 64), ncu --metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum: constant on the left 16.93 MB read, 0
+    # written; on the right 17.45 MB read, 0.57 MB written -- the chain operand (16.78 MB as
+    # FP32 pairs) once plus the constant's slices; weighted by the sweep's launch mix (84 : 44)
+    "gemm_tc.cu": ("d46901a1d0516b2d", 17.30e6),
+    # k_flip_df<false> (the FP32-pipe fold used at N = 64), same configuration (one slice of
+    # 256 chains x 2 spins): 16.86 MB read (G as FP32 pairs, once), 0 written (stays in L2)
+    "flip.cu": ("e3dbf5ad0522864f", 16.86e6),
 }
 
 
@@ -440,6 +448,9 @@ def main():  # noqa: C901
                     help="requests in the serving leg (0 = skip)")
     ap.add_argument("--plan-only", action="store_true",
                     help="print each rank's plan (device, chain range) and exit; no GPU work")
+    ap.add_argument("--sweeps-only", action="store_true",
+                    help="time the paths only (no peak probes, e2e, latency or serving legs): "
+                         "the command the ncu launch lists are taken from")
     args = ap.parse_args()
     if "WORLD_SIZE" not in os.environ and args.gpus > 1 and args.impl == "ours":
         sys.exit(relaunch_under_torchrun(args.gpus))
@@ -492,7 +503,9 @@ def main():  # noqa: C901
     nmc.load()
     stream = torch.cuda.current_stream()
     flush_buf = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    peaks = probe_peaks(nmc, torch, stream)
+    peaks = (dict(NOMINAL_TFLOPS, bf16=BF16_PEAK, bf16_sustained=BF16_PEAK_SUSTAINED,
+                  source="nominal (--sweeps-only)") if args.sweeps_only
+             else probe_peaks(nmc, torch, stream))
 
     def max_host(v):
         t = torch.tensor([float(v)], dtype=torch.float64)
@@ -543,15 +556,17 @@ def main():  # noqa: C901
                   "count": "step_flop(): wraps, stack products, recompute, QR, T update, "
                            "measurement and delayed updates, per sweep"}
 
-    e2e_dt, h2d, d2h, _ = run_e2e(nmc, torch, best, args.steps, rank, stream)
-    e2e = {"value": flips_per_step * args.steps / e2e_dt * world, "unit": UNIT,
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "path": best, "includes": "set_fields(host) + stack build + K sweeps + "
-                                     "measure(host) + get_fields(host)"}
+    e2e = None
+    if not args.sweeps_only:
+        e2e_dt, h2d, d2h, _ = run_e2e(nmc, torch, best, args.steps, rank, stream)
+        e2e = {"value": flips_per_step * args.steps / e2e_dt * world, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "path": best, "includes": "set_fields(host) + stack build + K sweeps + "
+                                         "measure(host) + get_fields(host)"}
 
     latency = None
     serve = None
-    if world == 1:
+    if world == 1 and not args.sweeps_only:
         latency = {p: run_latency(nmc, torch, stream, p) for p in ("fp64", "split_bf16")}
         if args.serve_requests > 0:
             from paper_2106_00712_gb300.serving import serve_stream
@@ -564,7 +579,7 @@ def main():  # noqa: C901
             dist.destroy_process_group()
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not args.sweeps_only:
         n_sw = 24
         v, dt = oracle_rate(cores, n_sw, 0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
