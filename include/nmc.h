@@ -195,6 +195,25 @@ nmc_status nmc_sweep_replay(nmc_ctx* ctx, const uint8_t* accept, size_t n, int m
  * observable is entry k / entry 5. *n_sweeps receives the number recorded. */
 nmc_status nmc_series(nmc_ctx* ctx, double* out, long long max_sweeps, long long* n_sweeps);
 
+/* Per-sweep accumulators of measured sweeps first .. first + count - 1 (host out, double
+ * [count][n_chains][8], the layout of nmc_series). NMC_EINVAL beyond the recorded sweeps. */
+nmc_status nmc_series_range(nmc_ctx* ctx, long long first, long long count, double* out);
+
+/* Start the listed chains afresh while the others keep running (the admission step of the
+ * serving loop, which packs independent requests into one context). chains: n distinct
+ * local chain indices; global_ids: their new global indices (Philox counter word 2, < 2^32).
+ * Each listed chain gets the Philox initial field of its global index (tag 1), its sweep
+ * numbering (Philox counter word 1) restarts at 0 with the next sweep, its sign is set to +1
+ * and its acceptance counts and drift are cleared; its per-sweep accumulators are those of
+ * the sweeps from then on. Then the UDV stacks and G of every chain are rebuilt from the
+ * fields, which reproduces the running chains' state exactly. So a restarted chain follows
+ * the same trajectory as the same global chain started alone in a fresh context. Only between
+ * sweep pairs: NMC_ESTATE after an odd number of sweeps since the fields were set (the next
+ * sweep must ascend), or before any fields; NMC_EINVAL for bad or repeated chains. Device
+ * work on the context stream; returns when it is done. */
+nmc_status nmc_restart_chains(nmc_ctx* ctx, const int* chains, const long long* global_ids,
+                              int n);
+
 /* Reduce the accumulators. per_chain: array of n_chains (or NULL); pooled: one (or
  * NULL). Pooled means are averages of per-chain means; errors as in nmc_est. */
 nmc_status nmc_measure(nmc_ctx* ctx, nmc_obs* per_chain, nmc_obs* pooled);

@@ -67,8 +67,10 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
   T* Gg = f.G + (long long)c * ns * NN;
   T* G = f.g_in_smem ? Gs : Gg;
   int8_t* fl = f.fields + ((long long)c * f.L + f.l) * N;
-  const uint32_t gchain = (uint32_t)(f.chain_offset + c);
-  const uint32_t sweep = f.ctr ? (uint32_t)f.ctr[0] : f.sweep;
+  // Philox counter words of this chain: its global index, and sweeps since its start
+  const uint32_t gchain = (uint32_t)(f.chain_id ? f.chain_id[c] : f.chain_offset + c);
+  const uint32_t sweep = (uint32_t)((f.ctr ? f.ctr[0] : (long long)f.sweep) -
+                                    (f.sweep_base ? f.sweep_base[c] : 0));
   const uint8_t* rp = f.replay ? f.replay + ((long long)c * f.L + f.l) * N : nullptr;
 
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -373,8 +375,10 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
   df2* Gg = f.G + (long long)c * ns * NN;
   df2* G = f.g_in_smem ? Gs : Gg;
   int8_t* fl = f.fields + ((long long)c * f.L + f.l) * N;
-  const uint32_t gchain = (uint32_t)(f.chain_offset + c);
-  const uint32_t sweep = f.ctr ? (uint32_t)f.ctr[0] : f.sweep;
+  // Philox counter words of this chain: its global index, and sweeps since its start
+  const uint32_t gchain = (uint32_t)(f.chain_id ? f.chain_id[c] : f.chain_offset + c);
+  const uint32_t sweep = (uint32_t)((f.ctr ? f.ctr[0] : (long long)f.sweep) -
+                                    (f.sweep_base ? f.sweep_base[c] : 0));
   const uint8_t* rp = f.replay ? f.replay + ((long long)c * f.L + f.l) * N : nullptr;
 
   for (int i = threadIdx.x; i < N; i += blockDim.x) {

@@ -23,6 +23,41 @@ __global__ void k_init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0
   }
 }
 
+__global__ void k_init_fields_list(int8_t* s, int L, int N, uint32_t k0, uint32_t k1,
+                                   const int* list, const long long* ids, int n) {
+  const long long per = (long long)L * N, total = per * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long j = e / per;
+    const uint32_t li = (uint32_t)(e - j * per);  // l*N + i
+    uint32_t ctr[4] = {li, 0u, (uint32_t)ids[j], kTagInit};
+    philox4x32_10(ctr, k0, k1);
+    s[(long long)list[j] * per + li] = (ctr[0] >> 31) ? (int8_t)-1 : (int8_t)1;
+  }
+}
+
+__global__ void k_restart_chain_state(const int* list, const long long* ids, int n,
+                                      long long sweep, long long* chain_id,
+                                      long long* sweep_base, double* sign,
+                                      unsigned long long* counts, unsigned long long* drift) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int c = list[j];
+  chain_id[c] = ids[j];
+  sweep_base[c] = sweep;
+  sign[c] = 1.0;
+  counts[3 * c] = counts[3 * c + 1] = counts[3 * c + 2] = 0ull;
+  drift[c] = 0ull;
+}
+
+__global__ void k_default_chain_ids(long long* chain_id, long long* sweep_base, int n,
+                                    long long offset) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  chain_id[c] = offset + c;
+  sweep_base[c] = 0;
+}
+
 __global__ void k_identity(double* U, double* D, double* T, int N, int batch) {
   const long long NN = (long long)N * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NN * batch;
@@ -215,6 +250,28 @@ void allow_max_dynamic_smem(const void* func) {
     done.insert({func, dev});
   else
     cudaGetLastError();
+}
+
+void init_fields_list(int8_t* s, int L, int N, uint32_t k0, uint32_t k1, const int* list,
+                      const long long* ids, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  k_init_fields_list<<<grid_for((long long)n * L * N), 256, 0, st>>>(s, L, N, k0, k1, list,
+                                                                     ids, n);
+}
+
+void restart_chain_state(const int* list, const long long* ids, int n, long long sweep,
+                         long long* chain_id, long long* sweep_base, double* sign,
+                         unsigned long long* counts, unsigned long long* drift,
+                         cudaStream_t st) {
+  if (n <= 0) return;
+  k_restart_chain_state<<<(n + 127) / 128, 128, 0, st>>>(list, ids, n, sweep, chain_id,
+                                                         sweep_base, sign, counts, drift);
+}
+
+void default_chain_ids(long long* chain_id, long long* sweep_base, int n_chains,
+                       long long offset, cudaStream_t st) {
+  k_default_chain_ids<<<(n_chains + 127) / 128, 128, 0, st>>>(chain_id, sweep_base, n_chains,
+                                                             offset);
 }
 
 void init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0, uint32_t k1,

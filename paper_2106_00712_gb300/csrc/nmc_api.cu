@@ -60,7 +60,7 @@ struct UDTView {
   long long sT;
 };
 
-constexpr uint64_t kCkptMagic = 0x4e4d43434b505431ull;  // "NMCCKPT1"
+constexpr uint64_t kCkptMagic = 0x4e4d43434b505432ull;  // "NMCCKPT2"
 constexpr int kNumClasses = 8;
 
 // One sweep direction (and measuring or not) recorded as a CUDA graph. The recorded launches
@@ -120,6 +120,10 @@ struct nmc_ctx {
   long long series_cap = 0, n_series = 0;
   uint8_t* dReplay = nullptr;
   long long* dCtr = nullptr;   // device mirrors: [0] sweep_counter, [1] n_series, [2] n_hist
+  // per chain: global index (Philox word 2) and the sweep counter at its start (word 1 counts
+  // sweeps since then); staging for the chain lists of nmc_restart_chains
+  long long *dChainId = nullptr, *dSweepBase = nullptr, *dIds = nullptr;
+  int* dList = nullptr;
   std::vector<void*> allocs;
 
   // sweeps replayed as CUDA graphs: [up, down][warm-up, measuring]
@@ -253,6 +257,8 @@ void free_all(nmc_ctx* x) {
   x->series_cap = x->n_series = 0;
   x->dReplay = nullptr;
   x->dCtr = nullptr;
+  x->dChainId = x->dSweepBase = x->dIds = nullptr;
+  x->dList = nullptr;
   x->configured = false;
   x->have_fields = false;
 }
@@ -358,6 +364,10 @@ nmc_status alloc_all(nmc_ctx* x) {
   NMC_TRY(dalloc(x, &x->dHist, x->hist_cap));
   NMC_TRY(dalloc(x, &x->dCtr, 3));
   NMC_TRY(dalloc(x, &x->dErr, 1));
+  NMC_TRY(dalloc(x, &x->dChainId, x->chains()));
+  NMC_TRY(dalloc(x, &x->dSweepBase, x->chains()));
+  NMC_TRY(dalloc(x, &x->dIds, x->chains()));
+  NMC_TRY(dalloc(x, &x->dList, x->chains()));
   if (x->dry) return NMC_OK;
 
   cudaStream_t st = x->st();
@@ -553,16 +563,22 @@ void flip(nmc_ctx* x, int l, const uint8_t* replay) {
                     (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
                     x->dCounts, replay, nullptr, split(dm), split(dp), x->ns(), x->dCtr};
     f.tc_fold = x->tc() ? 1 : 0;
+    f.chain_id = x->dChainId;
+    f.sweep_base = x->dSweepBase;
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   } else if (x->fp32()) {
     FlipArgs<float> f{x->dGf, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                       (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
                       x->dCounts, replay, nullptr, df2{0.f, 0.f}, df2{0.f, 0.f}, x->ns(), x->dCtr};
+    f.chain_id = x->dChainId;
+    f.sweep_base = x->dSweepBase;
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   } else {
     FlipArgs<double> f{x->dG, x->dS, x->N, x->Lt, l, x->kk, x->g_in_smem, k0, k1,
                        (uint32_t)x->sweep_counter, x->opt.chain_offset, dm, dp, x->dSign,
                        x->dCounts, replay, nullptr, df2{0.f, 0.f}, df2{0.f, 0.f}, x->ns(), x->dCtr};
+    f.chain_id = x->dChainId;
+    f.sweep_base = x->dSweepBase;
     launch(x, KC_FLIP, [&] { flip_slice(f, x->chains(), x->st()); });
   }
 }
@@ -759,6 +775,7 @@ nmc_status reset_chain_state(nmc_ctx* x) {
   NMC_CUDA(x, cudaMemsetAsync(x->dCounts, 0, 3 * sizeof(unsigned long long) * x->chains(), st));
   NMC_CUDA(x, cudaMemsetAsync(x->dDrift, 0, sizeof(unsigned long long) * x->chains(), st));
   NMC_CUDA(x, cudaMemsetAsync(x->dHist, 0, sizeof(unsigned long long) * x->hist_cap, st));
+  default_chain_ids(x->dChainId, x->dSweepBase, x->chains(), x->opt.chain_offset, st);
   x->n_hist = 0;
   x->n_series = 0;
   NMC_TRY(push_counters(x));
@@ -1316,7 +1333,8 @@ nmc_status nmc_get_dims(const nmc_ctx* x, int* N, int* L_tau, int* n_chains, int
 }
 
 // checkpoint layout: u64 magic, i64 N, Lt, chains, seed, sweep_counter, phase, n_series,
-// precision; then fields (int8), sign (f64), counts (u64 x3), drift (u64), series (f64)
+// precision; then fields (int8), sign (f64), counts (u64 x3), drift (u64), chain ids (i64),
+// sweep bases (i64), series (f64)
 nmc_status nmc_checkpoint(nmc_ctx* x, void* buf, size_t* n) {
   if (!x || !n) return NMC_EINVAL;
   if (!x->have_fields) return fail(x, NMC_ESTATE, "no fields set");
@@ -1325,7 +1343,7 @@ nmc_status nmc_checkpoint(nmc_ctx* x, void* buf, size_t* n) {
   const size_t nser = (size_t)x->n_series * C * 8;
   const size_t hdr = 9 * sizeof(int64_t);
   const size_t total = hdr + nf + C * sizeof(double) + 3 * C * sizeof(uint64_t) +
-                       C * sizeof(uint64_t) + nser * sizeof(double);
+                       C * sizeof(uint64_t) + 2 * C * sizeof(int64_t) + nser * sizeof(double);
   if (!buf) { *n = total; return NMC_OK; }
   if (*n < total) return fail(x, NMC_EINVAL, "nmc_checkpoint: buffer too small");
   NMC_CUDA(x, cudaSetDevice(x->device));
@@ -1343,6 +1361,10 @@ nmc_status nmc_checkpoint(nmc_ctx* x, void* buf, size_t* n) {
   p += 3 * C * sizeof(uint64_t);
   NMC_CUDA(x, cudaMemcpyAsync(p, x->dDrift, C * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
   p += C * sizeof(uint64_t);
+  NMC_CUDA(x, cudaMemcpyAsync(p, x->dChainId, C * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  p += C * sizeof(int64_t);
+  NMC_CUDA(x, cudaMemcpyAsync(p, x->dSweepBase, C * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  p += C * sizeof(int64_t);
   if (nser)
     NMC_CUDA(x, cudaMemcpyAsync(p, x->dSeries, nser * sizeof(double), cudaMemcpyDeviceToHost, st));
   NMC_CUDA(x, cudaStreamSynchronize(st));
@@ -1363,7 +1385,8 @@ nmc_status nmc_restore(nmc_ctx* x, const void* buf, size_t n) {
   const size_t nf = (size_t)C * x->Lt * x->N;
   const long long ns = h[7];
   const size_t nser = (size_t)ns * C * 8;
-  const size_t total = hdr + nf + C * sizeof(double) + 4 * C * sizeof(uint64_t) + nser * sizeof(double);
+  const size_t total = hdr + nf + C * sizeof(double) + 4 * C * sizeof(uint64_t) +
+                       2 * C * sizeof(int64_t) + nser * sizeof(double);
   if (n < total) return fail(x, NMC_EINVAL, "nmc_restore: truncated");
   const char* p = (const char*)buf + hdr;
   if (!valid_fields((const int8_t*)p, nf)) return fail(x, NMC_EINVAL, "nmc_restore: bad fields");
@@ -1378,6 +1401,10 @@ nmc_status nmc_restore(nmc_ctx* x, const void* buf, size_t n) {
   p += 3 * C * sizeof(uint64_t);
   NMC_CUDA(x, cudaMemcpyAsync(x->dDrift, p, C * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
   p += C * sizeof(uint64_t);
+  NMC_CUDA(x, cudaMemcpyAsync(x->dChainId, p, C * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  p += C * sizeof(int64_t);
+  NMC_CUDA(x, cudaMemcpyAsync(x->dSweepBase, p, C * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  p += C * sizeof(int64_t);
   NMC_CUDA(x, cudaStreamSynchronize(st));
   NMC_TRY(ensure_series(x, ns));
   if (nser)
@@ -1461,6 +1488,57 @@ nmc_status nmc_kernel_stats(nmc_ctx* x, nmc_kernel_stat* out, int max, int* n, i
   if (n) *n = KC_COUNT;
   if (reset)
     for (int c = 0; c < KC_COUNT; ++c) x->launches[c] = x->timed[c] = 0, x->total_ms[c] = 0;
+  return NMC_OK;
+}
+
+nmc_status nmc_restart_chains(nmc_ctx* x, const int* chains, const long long* global_ids,
+                              int n) {
+  if (!x || n < 0 || (n > 0 && (!chains || !global_ids))) return NMC_EINVAL;
+  if (!x->have_fields) return fail(x, NMC_ESTATE, "nmc_restart_chains before fields were set");
+  if (x->phase % 2) return fail(x, NMC_ESTATE, "nmc_restart_chains between the sweeps of a pair");
+  if (n > x->chains()) return fail(x, NMC_EINVAL, "nmc_restart_chains: more chains than held");
+  std::vector<char> seen(x->chains(), 0);
+  for (int j = 0; j < n; ++j) {
+    if (chains[j] < 0 || chains[j] >= x->chains() || seen[chains[j]] || global_ids[j] < 0 ||
+        global_ids[j] > 0xffffffffll)
+      return fail(x, NMC_EINVAL, "nmc_restart_chains: bad or repeated chain, or id outside 32 bits");
+    seen[chains[j]] = 1;
+  }
+  NMC_TRY(ensure_configured(x));
+  cudaStream_t st = x->st();
+  if (n > 0) {
+    NMC_CUDA(x, cudaMemcpyAsync(x->dList, chains, n * sizeof(int), cudaMemcpyHostToDevice, st));
+    NMC_CUDA(x, cudaMemcpyAsync(x->dIds, global_ids, n * sizeof(long long),
+                                cudaMemcpyHostToDevice, st));
+    launch(x, KC_OTHER, [&] {
+      init_fields_list(x->dS, x->Lt, x->N, (uint32_t)(x->seed & 0xffffffffu),
+                       (uint32_t)(x->seed >> 32), x->dList, x->dIds, n, st);
+    });
+    launch(x, KC_OTHER, [&] {
+      restart_chain_state(x->dList, x->dIds, n, x->sweep_counter, x->dChainId, x->dSweepBase,
+                          x->dSign, x->dCounts, x->dDrift, st);
+    });
+  }
+  // every chain's stacks and G from its fields: at an even phase this is exactly the state
+  // the last (descending) sweep left for the chains that keep running
+  build_stacks(x, true);
+  x->direct_since_build = 0;
+  NMC_CUDA(x, cudaGetLastError());
+  NMC_CUDA(x, cudaStreamSynchronize(st));
+  return NMC_OK;
+}
+
+nmc_status nmc_series_range(nmc_ctx* x, long long first, long long count, double* out) {
+  if (!x || first < 0 || count < 0 || (count > 0 && !out)) return NMC_EINVAL;
+  if (first + count > x->n_series)
+    return fail(x, NMC_EINVAL, "nmc_series_range: beyond the measured sweeps");
+  if (count == 0) return NMC_OK;
+  NMC_CUDA(x, cudaSetDevice(x->device));
+  const size_t per = (size_t)x->chains() * 8;
+  NMC_CUDA(x, cudaMemcpyAsync(out, x->dSeries + (size_t)first * per,
+                              (size_t)count * per * sizeof(double), cudaMemcpyDeviceToHost,
+                              x->st()));
+  NMC_CUDA(x, cudaStreamSynchronize(x->st()));
   return NMC_OK;
 }
 

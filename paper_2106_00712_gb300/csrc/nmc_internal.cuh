@@ -167,6 +167,8 @@ struct FlipArgs {
   int ns;                    // 2 spins, or 1: spin up only, G_dn = I - P G_up^T P
   const long long* ctr;      // device counters (ctr[0] = sweep counter) or null: use sweep
   int tc_fold = 0;           // compensated mode: 1 = rank-k fold may use the tensor cores
+  const long long* chain_id = nullptr;    // per chain: global index (Philox word 2), or null
+  const long long* sweep_base = nullptr;  // per chain: sweep counter at its start, or null
 };
 template <typename T> void flip_slice(const FlipArgs<T>& f, int n_chains, cudaStream_t st);
 size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem, int ns);
@@ -179,6 +181,19 @@ void allow_max_dynamic_smem(const void* func);
 void prefer_max_shared_carveout(const void* func);
 void init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0, uint32_t k1,
                  long long chain_offset, cudaStream_t st);
+// Philox initial fields (tag 1) of the listed chains only: chain list[j] gets global index
+// ids[j] (both device arrays of n entries).
+void init_fields_list(int8_t* s, int L, int N, uint32_t k0, uint32_t k1, const int* list,
+                      const long long* ids, int n, cudaStream_t st);
+// Start the listed chains afresh: chain_id = ids, sweep_base = sweep, sign = +1, counts and
+// drift cleared (device arrays of n entries; sign/counts/drift indexed by chain).
+void restart_chain_state(const int* list, const long long* ids, int n, long long sweep,
+                         long long* chain_id, long long* sweep_base, double* sign,
+                         unsigned long long* counts, unsigned long long* drift,
+                         cudaStream_t st);
+// chain_id[c] = offset + c, sweep_base[c] = 0 for every chain.
+void default_chain_ids(long long* chain_id, long long* sweep_base, int n_chains,
+                       long long offset, cudaStream_t st);
 void set_identity_batch(double* U, double* D, double* T, int N, int batch, cudaStream_t st);
 void copy_to_float(const double* x, float* y, long long n, cudaStream_t st);
 void copy_to_double(const float* x, double* y, long long n, cudaStream_t st);

@@ -28,6 +28,7 @@ EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_field
             "nmc_checkpoint", "nmc_restore", "nmc_expk", "nmc_series", "nmc_philox", "nmc_philox_device",
             "nmc_drift_history", "nmc_profile", "nmc_kernel_stats", "nmc_graph_stats",
             "nmc_green_noalloc", "nmc_debug_fail_alloc", "nmc_fma_probe", "nmc_debug_product",
+            "nmc_restart_chains", "nmc_series_range",
             "nmc_last_error",
             "nmc_version", "nmc_destroy")
 
@@ -126,6 +127,8 @@ def load():
         "nmc_green_noalloc": (i, [i, i, i, d, vp, vp, i, vp, vp]),
         "nmc_debug_fail_alloc": (None, [ctypes.c_longlong]),
         "nmc_fma_probe": (i, [i, i, i, i, vp, vp]),
+        "nmc_restart_chains": (i, [vp, vp, vp, i]),
+        "nmc_series_range": (i, [vp, ctypes.c_longlong, ctypes.c_longlong, vp]),
         "nmc_debug_product": (i, [i, i, i, i, vp, vp, vp, i, i, i, i, d, vp, vp]),
         "nmc_last_error": (ctypes.c_char_p, [vp]),
         "nmc_version": (ctypes.c_char_p, []),
@@ -387,6 +390,24 @@ def nmc_debug_product(precision, cst, X, const_is_a, fields=None, br=0, bc=0, cr
     return C
 
 
+def nmc_restart_chains(ctx, chains, global_ids):
+    """Start the given local chains afresh with the given global chain indices."""
+    c = np.ascontiguousarray(chains, dtype=np.int32)
+    g = np.ascontiguousarray(global_ids, dtype=np.int64)
+    if c.shape != g.shape:
+        raise ValueError("chains and global_ids differ in length")
+    _check(ctx, load().nmc_restart_chains(ctx, _ptr(c), _ptr(g), int(c.size)))
+
+
+def nmc_series_range(ctx, first, count):
+    """Per-sweep accumulators of measured sweeps first .. first + count - 1:
+    float64 [count][n_chains][8]."""
+    _, _, C, _ = nmc_get_dims(ctx)
+    out = np.zeros((int(count), C, 8))
+    _check(ctx, load().nmc_series_range(ctx, int(first), int(count), _ptr(out)))
+    return out
+
+
 def nmc_destroy(ctx):
     load().nmc_destroy(ctx)
 
@@ -489,6 +510,12 @@ class Context:
 
     def graph_stats(self):
         return nmc_graph_stats(self.ctx)
+
+    def restart_chains(self, chains, global_ids):
+        nmc_restart_chains(self.ctx, chains, global_ids)
+
+    def series_range(self, first, count):
+        return nmc_series_range(self.ctx, first, count)
 
 
 # ------------------------------------------------------------------ generator (nmc_gen.h)

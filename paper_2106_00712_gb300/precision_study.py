@@ -13,6 +13,7 @@ reduced-precision mode:
   combined standard error (across chains).
 
 Usage: python -m paper_2106_00712_gb300.precision_study [--sweeps 8] [--warm 2]
+                                                       [--U 2,4,8] [--modes fp32,split_bf16]
 Prints one JSON object.
 """
 import argparse
@@ -39,7 +40,7 @@ def _obs(o):
             for k in ("energy", "double_occ", "s_pipi")}
 
 
-def study_one(wl, U, n_warm, n_meas):
+def study_one(wl, U, n_warm, n_meas, modes=tuple(MODES)):
     out = {"U": U}
     t0 = time.perf_counter()
     ref = _ctx(wl, U, nmc.NMC_FP64)
@@ -53,7 +54,8 @@ def study_one(wl, U, n_warm, n_meas):
                    "drift_history_max": float(ref.drift_history().max())}
     ref.close()
     accepts = [(fields[s + 1] != fields[s]).astype(np.uint8) for s in range(len(fields) - 1)]
-    for name, prec in MODES.items():
+    for name in modes:
+        prec = MODES[name]
         row = {}
         c = _ctx(wl, U, prec)
         c.generate()
@@ -93,11 +95,15 @@ def main():
     ap.add_argument("--sweeps", type=int, default=6)
     ap.add_argument("--warm", type=int, default=2)
     ap.add_argument("--U", default="2,4,8")
+    ap.add_argument("--modes", default=",".join(MODES),
+                    help="reduced-precision modes to compare with the FP64 run")
     args = ap.parse_args()
+    modes = [m for m in args.modes.split(",") if m]
     wl = SQUARE_16x16
     report = {"workload": "hubbard-16x16-beta8-dtau0.05-nwrap8-k32-32chains",
               "sweeps": args.sweeps, "warm": args.warm,
-              "results": [study_one(wl, float(U), args.warm, args.sweeps)
+              "modes": modes,
+              "results": [study_one(wl, float(U), args.warm, args.sweeps, modes)
                           for U in args.U.split(",")]}
     print(json.dumps(report))
 

@@ -1,12 +1,16 @@
-"""Continuous batching on the GPU: each request's result is the same alone and in the mix.
+"""Continuous batching on the GPU: requests packed into shared pools give each request the
+result it gets alone.
 
-Eight requests of different lattice sizes, temperatures and couplings run (a) one at a
-time and (b) all in flight together on separate streams; the per-request observables must
-agree to 1e-12 (each request's chains have their own seed and context, and the compensated
-path makes the same decisions whatever runs beside it)."""
+Library level: chains started afresh inside a running context (nmc_restart_chains) follow
+exactly the trajectory of the same global chains in a fresh context -- and the oracle's --
+while the other chains of the context continue undisturbed. Serving level: eight requests
+(three sharing a problem) run (a) one at a time and (b) together through the pooled loop;
+every request's observables agree exactly, whichever pool and slot it landed in."""
+import numpy as np
 import pytest
 
-from paper_2106_00712_gb300.serving import GpuBackend, Request, Server, report
+from oracle.dqmc import Chain, Model, initial_fields
+from paper_2106_00712_gb300.serving import GpuPoolBackend, Request, Server, report
 
 pytestmark = pytest.mark.gpu
 
@@ -18,40 +22,78 @@ def backend():
         pytest.skip("no CUDA device")
     import __graft_entry__
     __graft_entry__.build()
-    return GpuBackend(precision=2)
+    return GpuPoolBackend(precision=2)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_restarted_chains_follow_fresh_chains(backend, prec):
+    from paper_2106_00712_gb300 import nmc
+    model = Model(4, 4, 1.0, 4.0, 1.0, 0.1, 5, seed=77)
+
+    def ctx(n):
+        c = nmc.Context(4, 4, 1.0, 4.0, 1.0, 0.1, 5, seed=77, n_chains=n, precision=prec)
+        c.generate()
+        return c
+
+    with ctx(4) as a, ctx(2) as b, ctx(4) as c:
+        a.sweep(4, measure=1)
+        with pytest.raises(nmc.NmcError):     # only between sweep pairs
+            a.sweep(1, measure=1)
+            a.restart_chains([1], [9])
+        a.sweep(1, measure=1)                 # back to an even phase (6 sweeps)
+        a.restart_chains([1, 2], [50, 51])
+        b.restart_chains([0, 1], [50, 51])
+        a.sweep(4, measure=1)
+        b.sweep(4, measure=1)
+        c.sweep(10, measure=1)
+        fa, fb, fc = a.fields(), b.fields(), c.fields()
+        np.testing.assert_array_equal(fa[1:3], fb)            # restarted = fresh
+        np.testing.assert_array_equal(fa[[0, 3]], fc[[0, 3]])  # the others undisturbed
+        for k in range(2):
+            for sp in (0, 1):
+                np.testing.assert_array_equal(a.green(1 + k, sp), b.green(k, sp))
+        np.testing.assert_array_equal(a.series_range(6, 4)[:, 1:3], b.series_range(0, 4))
+        np.testing.assert_array_equal(a.green(3, 1), c.green(3, 1))
+        # the fresh global chains are the oracle's chains 50 and 51
+        for k, gid in enumerate((50, 51)):
+            ref = Chain(model, initial_fields(model, gid), gid)
+            for _ in range(4):
+                ref.sweep(True)
+            np.testing.assert_array_equal(fb[k], ref.s)
 
 
 def _requests():
-    mix = [(4, 1.0, 2.0), (6, 2.0, 4.0), (8, 1.0, 8.0), (4, 2.0, 4.0), (6, 1.0, 2.0),
-           (8, 2.0, 4.0), (10, 1.0, 4.0), (6, 2.0, 8.0)]
-    return [Request(i, L, b, U, arrival=0.001 * i, chains=4, n_warm=2, n_meas=3,
-                    seed=100 + i) for i, (L, b, U) in enumerate(mix)]
+    mix = [(4, 1.0, 2.0), (6, 2.0, 4.0), (4, 1.0, 2.0), (8, 1.0, 8.0), (6, 1.0, 2.0),
+           (4, 1.0, 2.0), (10, 1.0, 4.0), (6, 2.0, 8.0)]
+    return [Request(i, L, b, U, arrival=0.002 * i, chains=4, n_warm=2, n_meas=4, n_wrap=5)
+            for i, (L, b, U) in enumerate(mix)]
 
 
 def test_results_same_alone_and_in_the_mix(backend):
     reqs = _requests()
     alone = {}
     for r in reqs:
-        srv = Server(backend, hbm_budget=1 << 40, chunk=2)
+        srv = Server(backend, hbm_budget=1 << 40, max_slots=4)
         res, _ = srv.run([r], realtime=False)
         alone[r.rid] = res[r.rid].obs
-    srv = Server(backend, hbm_budget=1 << 40, chunk=1)
-    mixed, makespan = srv.run(reqs, realtime=True)
+    srv = Server(backend, hbm_budget=1 << 40, max_slots=4)
+    mixed, makespan = srv.run(reqs, realtime=False)
     assert srv.peak_active >= 4
+    assert max(p["served"] for p in srv.pool_log) >= 3     # the three 4x4 requests share a pool
     for r in reqs:
         for k in ("energy", "double_occ", "s_pipi", "density"):
-            assert abs(mixed[r.rid].obs[k] - alone[r.rid][k]) < 1e-12, (r.rid, k)
-        assert mixed[r.rid].obs["max_drift"] <= 1e-5
+            assert mixed[r.rid].obs[k] == alone[r.rid][k], (r.rid, k)
+    assert max(p["max_drift"] for p in srv.pool_log) <= 1e-5
     rep = report(mixed, reqs, makespan)
     assert rep["p99_latency_s"] >= rep["p50_latency_s"] > 0
 
 
-def test_budget_limits_concurrency(backend):
-    reqs = [Request(i, 6, 1.0, 4.0, chains=4, n_warm=1, n_meas=2, seed=i) for i in range(4)]
-    one = backend.footprint(reqs[0])
-    srv = Server(backend, hbm_budget=one, chunk=2)
+def test_budget_limits_pools(backend):
+    reqs = [Request(i, 6, 1.0, 4.0, chains=4, n_warm=1, n_meas=3, n_wrap=5) for i in range(4)]
+    one = backend.footprint(reqs[0], 1, 2000)
+    srv = Server(backend, hbm_budget=one, max_slots=1)
     res, _ = srv.run(reqs, realtime=False)
-    assert srv.peak_active == 1 and len(res) == 4
+    assert srv.peak_pools == 1 and len(res) == 4
 
 
 def test_concurrent_contexts_match_alone_large_lattices(backend):
