@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
     }
     __syncthreads();
     if (s_accept[i & 1]) {
-      const T coef[2] = {(T)s_coef[0], (T)s_coef[1]};
+      const T coef0 = (T)s_coef[0], coef1 = (T)s_coef[1];
       for (int t = threadIdx.x; t < 2 * ns * N; t += blockDim.x) {
         const int sp = t / (2 * N);
         const int kind = (t / N) & 1;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
         if (kind == 0) {  // column i of G^: a_m = coef (e_i - G^_{:,i})
           T v = Gsp[(long long)r * N + i];
           for (int q = 0; q < m; ++q) v = fma(A_[q * N + r], B_[q * N + i], v);
-          Ap[(sp * KK + m) * N + r] = coef[sp] * ((r == i ? T(1) : T(0)) - v);
+          Ap[(sp * KK + m) * N + r] = (sp ? coef1 : coef0) * ((r == i ? T(1) : T(0)) - v);
         } else {          // row i of G^: b_m = G^_{i,:}
           T v = Gsp[(long long)i * N + r];
           for (int q = 0; q < m; ++q) v = fma(A_[q * N + i], B_[q * N + r], v);
@@ -202,7 +202,26 @@ __device__ void flush_df(df2* G, const df2* Ap, const df2* Bp, int m, int N, int
     const df2* B_ = Bp + sp * KK * N;
     df2* Gs = G + sp * NN;
     for (int c = c0; c < N; c += (nthr >= N ? N : nthr)) {
-      for (int r = (nthr >= N ? r0 : 0); r < N; r += rstep) {
+      int r = nthr >= N ? r0 : 0;
+      // four rows at a time: four independent accumulation chains share each B load
+      // (every output still sees the same operations in the same order)
+      for (; r + 3 * rstep < N; r += 4 * rstep) {
+        df2 a0 = Gs[r * N + c], a1 = Gs[(r + rstep) * N + c];
+        df2 a2 = Gs[(r + 2 * rstep) * N + c], a3 = Gs[(r + 3 * rstep) * N + c];
+        for (int q = 0; q < m; ++q) {
+          const df2 bq = B_[q * N + c];
+          const df2* Aq = A_ + q * N + r;
+          df_fma_acc(a0, Aq[0], bq);
+          df_fma_acc(a1, Aq[rstep], bq);
+          df_fma_acc(a2, Aq[2 * rstep], bq);
+          df_fma_acc(a3, Aq[3 * rstep], bq);
+        }
+        Gs[r * N + c] = df_finish(a0);
+        Gs[(r + rstep) * N + c] = df_finish(a1);
+        Gs[(r + 2 * rstep) * N + c] = df_finish(a2);
+        Gs[(r + 3 * rstep) * N + c] = df_finish(a3);
+      }
+      for (; r < N; r += rstep) {
         df2 acc = Gs[r * N + c];
         for (int q = 0; q < m; ++q) df_fma_acc(acc, A_[q * N + r], B_[q * N + c]);
         Gs[r * N + c] = df_finish(acc);
