@@ -20,6 +20,10 @@ namespace nmc {
 namespace {
 
 constexpr int kThreads = 256;
+// compensated kernel: 256 threads for the panel entries (one entry of G^'s column or row each
+// at N = 64) plus one warp whose first thread evaluates the ratio meanwhile
+constexpr int kPanelThreads = 256;
+constexpr int kThreadsDf = kPanelThreads + 32;
 
 // Thread t owns column c = t % N of rows t / N, t / N + rows_per_pass, ... of both spins:
 // 32-bit index arithmetic only, consecutive threads on consecutive columns.
@@ -46,7 +50,7 @@ __device__ void flush(T* G, const T* Ap, const T* Bp, int m, int N, int KK, long
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_flip(const FlipArgs<T> f) {
+__global__ void __launch_bounds__(kThreads, 2) k_flip(const FlipArgs<T> f) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_accept[2];  // by attempt parity: see the loop
   __shared__ double s_coef[2];
@@ -369,7 +373,7 @@ __device__ void flush_tc(df2* G, const df2* Ap, const df2* Bp, int m, int N, int
 // TC: fold on the tensor cores (flush_tc) instead of the double-float loop (flush_df); a
 // separate instantiation, so the FP32-pipe variant keeps its smaller register footprint.
 template <bool TC>
-__global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
+__global__ void __launch_bounds__(kThreadsDf, 2) k_flip_df(const FlipArgs<df2> f) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_accept[2];  // by attempt parity: see the loop
   __shared__ df2 s_coef[2];
@@ -426,24 +430,27 @@ __global__ void __launch_bounds__(kThreads) k_flip_df(const FlipArgs<df2> f) {
   // ratio's latency thus hides behind the panel products instead of adding to them. Flags
   // are double-buffered by attempt parity (see k_flip).
   const df2 one{1.f, 0.f};
-  const int rt = blockDim.x - 1;
+  const int rt = kPanelThreads;   // the ratio thread: lane 0 of the last warp
   int m = 0;
   for (int i = 0; i < N; ++i) {
-    for (int t = threadIdx.x; t < ns * N; t += blockDim.x) {
-      const int sp = t / N, r = t % N;
+    for (int t = threadIdx.x; t < 2 * ns * N && threadIdx.x < kPanelThreads;
+         t += kPanelThreads) {
+      const int kind = t / (ns * N), e = t - kind * ns * N;
+      const int sp = e / N, r = e % N;
       const df2* Gsp = G + sp * NN;
       const df2* A_ = Ap + sp * KK * N;
       const df2* B_ = Bp + sp * KK * N;
-      df2 ca = Gsp[(long long)r * N + i];   // column i of G^, row r
-      df2 rb = Gsp[(long long)i * N + r];   // row i of G^, column r
-      for (int q = 0; q < m; ++q) {
-        df_fma_acc(ca, A_[q * N + r], B_[q * N + i]);
-        df_fma_acc(rb, A_[q * N + i], B_[q * N + r]);
+      if (kind == 0) {   // column i of G^, row r
+        df2 ca = Gsp[(long long)r * N + i];
+        for (int q = 0; q < m; ++q) df_fma_acc(ca, A_[q * N + r], B_[q * N + i]);
+        df2 v = df_neg(df_finish(ca));
+        if (r == i) v = df_add(v, one);
+        Ap[(sp * KK + m) * N + r] = v;          // times the coefficient once accepted
+      } else {           // row i of G^, column r
+        df2 rb = Gsp[(long long)i * N + r];
+        for (int q = 0; q < m; ++q) df_fma_acc(rb, A_[q * N + i], B_[q * N + r]);
+        Bp[(sp * KK + m) * N + r] = df_finish(rb);
       }
-      df2 v = df_neg(df_finish(ca));
-      if (r == i) v = df_add(v, one);
-      Ap[(sp * KK + m) * N + r] = v;          // times the coefficient once accepted
-      Bp[(sp * KK + m) * N + r] = df_finish(rb);
     }
     if (threadIdx.x == rt) {
       const int s = sl[i];
@@ -550,10 +557,10 @@ void flip_slice<df2>(const FlipArgs<df2>& f, int n_chains, cudaStream_t st) {
   const size_t bytes = flip_smem_bytes(f.N, f.kk, sizeof(df2), f.g_in_smem, f.ns);
   if (f.tc_fold && f.kk <= kTcFlushMaxK && f.N >= kTcFlushMinN) {
     allow_max_dynamic_smem((const void*)k_flip_df<true>);
-    k_flip_df<true><<<n_chains, kThreads, bytes, st>>>(f);
+    k_flip_df<true><<<n_chains, kThreadsDf, bytes, st>>>(f);
   } else {
     allow_max_dynamic_smem((const void*)k_flip_df<false>);
-    k_flip_df<false><<<n_chains, kThreads, bytes, st>>>(f);
+    k_flip_df<false><<<n_chains, kThreadsDf, bytes, st>>>(f);
   }
 }
 

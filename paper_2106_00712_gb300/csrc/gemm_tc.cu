@@ -46,8 +46,10 @@ constexpr int kS = 7;            // slices per operand
 constexpr int kLoFirst = 3;      // first slice of the lo part of an FP32 pair
 constexpr int kAcc = kS;         // one accumulator per group g = s + t = 0..6
 constexpr int kM = 128;          // tile rows = tensor-memory lanes
-constexpr int kSlicers = 512;    // 16 warps: slicing and epilogue
-constexpr int kThreads = kSlicers + 32;   // + one warp issuing the TMA copies and the MMAs
+// SL = 512 slicing/epilogue threads (16 warps), column tiles up to 64, one CTA per SM (7 x 64
+// accumulator columns), plus one warp that issues the TMA copies and the MMAs. (A variant with
+// 256 slicing threads, column tiles of 32 and two CTAs per SM slices every row twice at N = 64;
+// it measured 44 us per launch against 35.)
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz: a bounded wait
 constexpr int kMaxTcN = 320;     // exactness of the group-2 sums needs K <= 340
 
@@ -261,8 +263,7 @@ __host__ __device__ inline uint32_t tmem_columns(int cols) {
   return cols <= 64 ? 64u : cols <= 128 ? 128u : cols <= 256 ? 256u : 512u;
 }
 
-constexpr int kKParts = kSlicers / kM;   // slicing threads per row of the tile (4)
-constexpr int kCache = 2;                // chunks of a row kept in registers (N <= 64)
+constexpr int kCache = 2;                // chunks of a row kept in registers
 
 // One (row tile, column tile) of D = A B^T. Slicing thread t (< 512) handles row
 // r = t % 128 of the tile and, in every K chunk, the 8-wide K group t / 128 (of KC / 8): it
@@ -271,9 +272,10 @@ constexpr int kCache = 2;                // chunks of a row kept in registers (N
 // of each full stage, and releases the stage when they complete. In the epilogue slicing
 // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its permitted quarter) and 16
 // columns starting at 16 (w / 4).
-template <bool CONST_A>
-__global__ void __launch_bounds__(kThreads, 1)
+template <bool CONST_A, int SL>
+__global__ void __launch_bounds__(SL + 32, SL == 512 ? 1 : 2)
     k_gemm_tc(const DfGemmArgs g, const TcGeom geo, const __grid_constant__ CUtensorMap tmap) {
+  constexpr int kKParts = SL / kM;   // slicing threads per row of the tile (4 or 2)
   extern __shared__ uint8_t smraw[];
   __shared__ uint64_t bar_tma[2], bar_mma[2], bar_full[2];
   __shared__ uint32_t tmem_base_sh;
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = g.N, NT = geo.NT, KC = geo.KC, n_chunks = geo.n_chunks;
   const int n_tile = blockIdx.y;
-  const bool mma_warp = warp == kSlicers / 32;
+  const bool mma_warp = warp == SL / 32;
   uint8_t* base = (uint8_t*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   // stage st: A slices at base + st * a_bytes, B slices at base + 2 a_bytes + st * b_bytes
   auto As = [&](int st) { return base + st * a_bytes(KC); };
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int k = 0; k < 2; ++k) {
       mbar_init(&bar_tma[k], 1);
       mbar_init(&bar_mma[k], 1);
-      mbar_init(&bar_full[k], kSlicers / 32);   // one arrival per slicing warp
+      mbar_init(&bar_full[k], SL / 32);   // one arrival per slicing warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_proxy_async();
@@ -312,9 +314,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   // this thread's row of the chain operand: matrix b, index i (a row of X, or a column of X
   // when the constant is on the left), and its K group within each chunk
-  // four consecutive lanes share a row (one K group each), so a warp reads eight rows'
-  // 256-byte runs and writes eight rows' 16-byte slice pieces into 512 contiguous bytes
-  const int r = (warp * 8 + (lane >> 2)) & (kM - 1), kp = lane & (kKParts - 1);
+  // kKParts consecutive lanes share a row (one 8-wide K group each), so a warp reads
+  // contiguous runs of its rows and writes their 16-byte slice pieces contiguously
+  const int r = (warp * (32 / kKParts) + lane / kKParts) & (kM - 1), kp = lane & (kKParts - 1);
   const bool kpart = !mma_warp && kp * 8 < KC;   // KC = 16: only two K groups per chunk
   const long long grow = (long long)blockIdx.x * kM + r;
   const bool valid = grow < geo.rows;
@@ -368,9 +370,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   }
-  // the row maximum over the row's four lanes
+  // the row maximum over the row's lanes
   mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  if (kKParts == 4) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
   if (!mma_warp && kp == 0) rexp[r] = row_exponent(mx);
   tc_fence_before();
   __syncthreads();
@@ -579,6 +581,7 @@ EncodeTiledFn encode_fn() {
 TcShape tc_shape(int N) {
   TcShape s{};
   s.N = N;
+  s.SL = 512;
   s.KC = N <= 16 ? 16 : 32;
   s.KP = (N + s.KC - 1) / s.KC * s.KC;
   s.n_chunks = s.KP / s.KC;
@@ -633,13 +636,12 @@ void gemm_tc(const DfGemmArgs& g, bool const_is_a, const void* tmap, int* err,
   if (smem < fit) smem = fit;
   const dim3 grid((unsigned)((geo.rows + kM - 1) / kM), (unsigned)s.n_tiles);
   const CUtensorMap& m = *(const CUtensorMap*)tmap;
-  if (const_is_a) {
-    allow_max_dynamic_smem((const void*)k_gemm_tc<true>);
-    k_gemm_tc<true><<<grid, kThreads, smem, st>>>(g, geo, m);
-  } else {
-    allow_max_dynamic_smem((const void*)k_gemm_tc<false>);
-    k_gemm_tc<false><<<grid, kThreads, smem, st>>>(g, geo, m);
-  }
+  auto run = [&](auto kernel, int threads) {
+    allow_max_dynamic_smem((const void*)kernel);
+    kernel<<<grid, threads, smem, st>>>(g, geo, m);
+  };
+  if (const_is_a) run(k_gemm_tc<true, 512>, 512 + 32);
+  else run(k_gemm_tc<false, 512>, 512 + 32);
 }
 
 }  // namespace nmc

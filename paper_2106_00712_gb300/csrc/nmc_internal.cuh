@@ -123,7 +123,7 @@ struct DfGemmArgs {
 void gemm_df(const DfGemmArgs& g, cudaStream_t st);
 // The same products on the tcgen05 tensor cores (accumulators in tensor memory, the constant's
 // slices copied by TMA), any N <= 320. Geometry of the tiling for a given N:
-struct TcShape { int N, NT, KC, KP, n_chunks, n_tiles; };
+struct TcShape { int N, NT, KC, KP, n_chunks, n_tiles, SL; };
 TcShape tc_shape(int N);
 bool gemm_tc_supported(int N);
 size_t tc_const_elems(int N);   // bf16 elements of one sliced constant (one orientation)

@@ -22,7 +22,11 @@ namespace nmc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+// Gauss-Jordan: 16 warps (rows over warps, columns over lanes), so a matrix alone on an SM
+// (the tail of a batch that does not fill the GPU in one wave) still has the warps to hide
+// the FP64 latency
+constexpr int kSolveThreads = 512;
+constexpr int kSolveWarps = kSolveThreads / 32;
 constexpr size_t kSmemLimit = 200 * 1024;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -215,7 +219,7 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kSolveThreads)
 k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long sUR,
         const double* __restrict__ DR, long long sDR, double* __restrict__ Y,
         double* __restrict__ ws, int N, int use_smem) {
@@ -229,7 +233,7 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
   const double* Xb = X + (long long)b * NN;
   const double* Ub = UR + (long long)b * sUR;
   const double* Dv = DR + (long long)b * sDR;
-  for (int e = tid; e < 2 * (int)NN; e += kThreads) {
+  for (int e = tid; e < 2 * (int)NN; e += kSolveThreads) {
     const int r = e / ld, c = e - r * ld;
     double v;
     if (c < N) v = Xb[r * N + c];
@@ -251,7 +255,7 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
     __syncthreads();
     const int piv = s_piv;
     if (piv != p) {
-      for (int c = p + tid; c < ld; c += kThreads) {
+      for (int c = p + tid; c < ld; c += kSolveThreads) {
         const double t = Aug[(long long)p * ld + c];
         Aug[(long long)p * ld + c] = Aug[(long long)piv * ld + c];
         Aug[(long long)piv * ld + c] = t;
@@ -259,10 +263,10 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
       __syncthreads();
     }
     const double inv = 1.0 / Aug[p * ld + p];
-    for (int c = p + 1 + tid; c < ld; c += kThreads) Aug[p * ld + c] *= inv;
+    for (int c = p + 1 + tid; c < ld; c += kSolveThreads) Aug[p * ld + c] *= inv;
     __syncthreads();
     // rows over warps, columns over lanes (32-bit indices)
-    for (int r = warp; r < N; r += kWarps) {
+    for (int r = warp; r < N; r += kSolveWarps) {
       if (r == p) continue;
       const double mlt = Aug[r * ld + p];
       for (int c = p + 1 + lane; c < ld; c += 32) Aug[r * ld + c] -= mlt * Aug[p * ld + c];
@@ -270,7 +274,7 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
     __syncthreads();
   }
   double* Yb = Y + (long long)b * NN;
-  for (int e = tid; e < (int)NN; e += kThreads) {
+  for (int e = tid; e < (int)NN; e += kSolveThreads) {
     const int r = e / N, c = e - r * N;
     Yb[e] = Aug[r * ld + N + c];
   }
@@ -294,7 +298,7 @@ void solve_stab(const double* X, const double* UR, long long sUR, const double* 
   const int use_smem = big <= kSmemLimit;
   const size_t bytes = use_smem ? big : 0;
   allow_max_dynamic_smem((const void*)k_solve);
-  k_solve<<<batch, kThreads, bytes, st>>>(X, UR, sUR, DR, sDR, Y, ws, N, use_smem);
+  k_solve<<<batch, kSolveThreads, bytes, st>>>(X, UR, sUR, DR, sDR, Y, ws, N, use_smem);
 }
 
 bool stab_needs_workspace(int N) {
