@@ -64,13 +64,13 @@ BF16_PEAK, BF16_PEAK_SUSTAINED = _measured_peaks_file()
 # capture time; reported as null once the source has changed.
 TRAFFIC = {
     # k_gemm_tc, bench launch configuration (512 products of 64 x 64), ncu --metrics
-    # dram__bytes_read.sum,dram__bytes_write.sum: constant on the left 16.93 MB read, 0
-    # written; on the right 17.45 MB read, 0.57 MB written -- the chain operand (16.78 MB as
+    # dram__bytes_read.sum,dram__bytes_write.sum: constant on the left 16.90 MB read, 0
+    # written; on the right 17.48 MB read, 0.57 MB written -- the chain operand (16.78 MB as
     # FP32 pairs) once plus the constant's slices; weighted by the sweep's launch mix (84 : 44)
-    "gemm_tc.cu": ("d46901a1d0516b2d", 17.30e6),
+    "gemm_tc.cu": ("617dd71437f9fc66", 17.29e6),
     # k_flip_df<false> (the FP32-pipe fold used at N = 64), same configuration (one slice of
-    # 256 chains x 2 spins): 16.86 MB read (G as FP32 pairs, once), 0 written (stays in L2)
-    "flip.cu": ("e3dbf5ad0522864f", 16.86e6),
+    # 256 chains x 2 spins): 16.89 MB read (G as FP32 pairs, once), 0 written (stays in L2)
+    "flip.cu": ("c3cfd2b90b8ad68f", 16.89e6),
 }
 
 
@@ -108,6 +108,8 @@ def class_rooflines(st, base, ns, acc, peaks, tc):
         launches, timed, ms = st[cls]
         return flop / (ms / max(timed, 1) * 1e-3) / 1e12
     def entry(bound, kernel, a, peak, src, **kw):
+        if "probe" in src and str(peaks.get("source", "")).startswith("nominal"):
+            src = src.split(", of measured")[0] + ", nominal figure (peaks not probed in this run)"
         return {"bound": bound, "kernel": kernel, "achieved": a, "peak": peak,
                 "unit": "TFLOP/s", "frac": a / peak, "peak_source": src, **kw}
     out = {}
