@@ -126,6 +126,12 @@ def class_rooflines(st, base, ns, acc, peaks, tc):
         out["gemm_df"] = entry("alu", "k_gemm_df<64,64> (compensated FP32 pairs)", a,
                                peaks["fp32"], "FP32 FMA probe (nmc_fma_probe), of measured",
                                frac_of_pair_ceiling=a / (peaks["fp32"] / PAIR_INSTR_PER_FMA))
+    if st.get("gemm_pair", (0,))[0]:
+        a = rate("gemm_pair", 2.0 * N ** 3 * batch)
+        out["gemm_pair"] = entry("alu", "k_gemm_pair<64,64> (FP64 stabilization products "
+                                 "accumulated in FP32 pairs)", a, peaks["fp32"],
+                                 "FP32 FMA probe (nmc_fma_probe), of measured",
+                                 frac_of_pair_ceiling=a / (peaks["fp32"] / PAIR_INSTR_PER_FMA))
     if st.get("gemm", (0,))[0]:
         kern = {"fp64": "k_gemm<double,64>", "fp32": "k_gemm<float,64>",
                 "fp32x2": "k_gemm<double,64> (FP64 recompute, T updates)"}[base]
@@ -268,19 +274,20 @@ def oracle_rate(cores, steps, warmup):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-# path name -> (nmc precision, particle-hole single spin)
-PATHS = {"fp64": (0, 0), "fp32": (1, 0), "split_bf16": (2, 0), "fp32x2": (4, 0),
-         "fp64_ph": (0, 1), "split_bf16_ph": (2, 1)}
+# path name -> (nmc precision, particle-hole single spin, stabilization products in FP32
+# pairs)
+PATHS = {"fp64": (0, 0, 0), "fp32": (1, 0, 0), "split_bf16": (2, 0, 0), "fp32x2": (4, 0, 0),
+         "fp64_ph": (0, 1, 0), "split_bf16_ph": (2, 1, 0), "split_bf16_sp": (2, 0, 1)}
 BASE = {0: "fp64", 1: "fp32", 2: "fp32x2", 4: "fp32x2"}   # arithmetic class of the SIMT parts
 
 
 def context(nmc, path, rank, stream, wl=WL, chains=None):
-    prec, ph = PATHS[path]
+    prec, ph, sp = PATHS[path]
     n = wl.n_chains if chains is None else chains
     return nmc.Context(wl.Lx, wl.Ly, wl.t, wl.U, wl.beta, wl.dtau, wl.n_wrap, seed=wl.seed,
                        n_chains=n, delay_k=wl.delay_k, precision=prec,
                        drift_tol=1e300, chain_offset=weak_offset(rank, n),
-                       stream=stream.cuda_stream, ph_symmetric=ph)
+                       stream=stream.cuda_stream, ph_symmetric=ph, stab_pairs=sp)
 
 
 def probe_peaks(nmc, torch, stream):
@@ -442,7 +449,8 @@ def main():  # noqa: C901
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", default="fp64,split_bf16,fp32x2,fp32,fp64_ph,split_bf16_ph")
+    ap.add_argument("--paths",
+                    default="fp64,split_bf16,fp32x2,fp32,fp64_ph,split_bf16_ph,split_bf16_sp")
     ap.add_argument("--value-paths", default="fp64,split_bf16,fp32x2,fp32",
                     help="paths eligible for `value` (the per-spin G of the specification)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -540,7 +548,7 @@ def main():  # noqa: C901
     st = r["stats"]
     dom = max(st, key=lambda k: st[k][2])          # kernel class with most device time
     launches_total = r["launches"]   # kernels launched in the timed (value) steps
-    prec, ph = PATHS[best]
+    prec, ph, _ = PATHS[best]
     ns = 1 if ph else 2
     base = BASE[prec]
     tot_ms = max(sum(x[2] for x in st.values()), 1e-30)

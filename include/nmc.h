@@ -97,6 +97,14 @@ typedef struct {
                             kernel; the same kernels with the same arguments, so the results
                             are identical); not while profiling or replaying decisions.
                             0: launch every kernel directly.                     default 1  */
+  int stab_pairs;        /* compensated precisions only (else NMC_EINVAL). 1: the products of
+                            the stabilization (the T updates of the UDT stacks and the three
+                            products of the recompute) take FP64 operands and give FP64
+                            results, but accumulate in FP32 pairs on the FP32 pipe (error-free
+                            products and sums, ~2^-44 of the sum of |a_ik b_kj|) instead of FP64
+                            FMAs; operands must lie within the FP32 range, which the stacks'
+                            D-split keeps them in. The QR and the Gauss-Jordan solve stay FP64.
+                            0: FP64 (SIMT FP64 pipe).                            default 0  */
 } nmc_options;
 
 typedef struct {
@@ -258,7 +266,8 @@ nmc_status nmc_philox_device(const uint32_t* d_c0, int n, uint32_t c1, uint32_t 
 nmc_status nmc_drift_history(nmc_ctx* ctx, double* out, long long max, long long* n);
 
 /* Per-kernel accounting (tracing). Every library kernel launch is counted by class
- * ("gemm", "flip", "qrp", "solve", "measure", "other", "gemm_df", "gemm_tc"). With profiling enabled, each
+ * ("gemm", "flip", "qrp", "solve", "measure", "other", "gemm_df", "gemm_tc", "gemm_pair"). With
+ * profiling enabled, each
  * launch is also bracketed by CUDA events on the context stream, and nmc_kernel_stats
  * reports the summed device time of the bracketed launches. */
 typedef struct {

@@ -61,7 +61,7 @@ struct UDTView {
 };
 
 constexpr uint64_t kCkptMagic = 0x4e4d43434b505432ull;  // "NMCCKPT2"
-constexpr int kNumClasses = 8;
+constexpr int kNumClasses = 16;   // capacity of the per-class counters (>= KC_COUNT)
 
 // One sweep direction (and measuring or not) recorded as a CUDA graph. The recorded launches
 // name the UDV stack buffers by pointer, and a sweep permutes those buffers, so a graph is
@@ -136,9 +136,9 @@ struct nmc_ctx {
 
   // per-kernel accounting: launch counts always, CUDA-event brackets when prof is set
   bool prof = false;
-  long long launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  long long timed[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  double total_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long launches[kNumClasses] = {};
+  long long timed[kNumClasses] = {};
+  double total_ms[kNumClasses] = {};
   struct Rec { int cls; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> event_pool;
@@ -175,10 +175,12 @@ nmc_status fail(nmc_ctx* x, nmc_status s, const std::string& msg) {
   } while (0)
 
 enum KernelClass {
-  KC_GEMM = 0, KC_FLIP, KC_QRP, KC_SOLVE, KC_MEASURE, KC_OTHER, KC_GEMM_DF, KC_GEMM_TC, KC_COUNT
+  KC_GEMM = 0, KC_FLIP, KC_QRP, KC_SOLVE, KC_MEASURE, KC_OTHER, KC_GEMM_DF, KC_GEMM_TC,
+  KC_GEMM_PAIR, KC_COUNT
 };
 const char* const kKernelClassNames[KC_COUNT] = {"gemm", "flip", "qrp", "solve", "measure",
-                                                 "other", "gemm_df", "gemm_tc"};
+                                                 "other", "gemm_df", "gemm_tc", "gemm_pair"};
+static_assert(KC_COUNT <= kNumClasses, "per-class counters too small");
 
 cudaEvent_t pool_event(nmc_ctx* x) {
   if (!x->event_pool.empty()) {
@@ -583,6 +585,14 @@ void flip(nmc_ctx* x, int l, const uint8_t* replay) {
   }
 }
 
+// The FP64 products of the stabilization (T updates, recompute): k_gemm on the FP64 pipe,
+// or, with nmc_options.stab_pairs, the same products accumulated in FP32 pairs
+void stab_gemm(nmc_ctx* x, const GemmArgs<double>& g) {
+  cudaStream_t st = x->st();
+  if (x->opt.stab_pairs) launch(x, KC_GEMM_PAIR, [&] { gemm_pair(g, st); });
+  else launch(x, KC_GEMM, [&] { gemm(g, st); });
+}
+
 // dst = QRP-UDT of (product of block j's B matrices) applied to src; right: B_block src,
 // left (transposed stack): B_block^T src.
 void stack_update(nmc_ctx* x, int j, const UDTView& src, const UDTBuf& dst, bool right) {
@@ -618,7 +628,7 @@ void stack_update(nmc_ctx* x, int j, const UDTView& src, const UDTBuf& dst, bool
       scur = NN;
     }
     launch(x, KC_QRP, [&] { qrp_udt(X, dst.U, dst.D, x->dTp, x->dWS, x->N, x->batch(), st); });
-    launch(x, KC_GEMM, [&] { gemm(gemm_base<double>(x, x->dTp, NN, src.T, src.sT, dst.T), st); });
+    stab_gemm(x, gemm_base<double>(x, x->dTp, NN, src.T, src.sT, dst.T));
     return;
   }
   if (right) {
@@ -660,13 +670,13 @@ void recompute(nmc_ctx* x, const UDTView& R, const UDTView& L, bool drift) {
   g1.transA = 1;
   g1.crow = vec_scale(R.D, R.sD, SC_INV_MAX1);
   g1.ccol = vec_scale(L.D, L.sD, SC_INV_MAX1);
-  launch(x, KC_GEMM, [&] { gemm(g1, st); });
+  stab_gemm(x, g1);
   auto g2 = gemm_base<double>(x, R.T, R.sT, L.T, L.sT, x->dXs);
   g2.transB = 1;
   g2.crow = vec_scale(R.D, R.sD, SC_MIN1);
   g2.ccol = vec_scale(L.D, L.sD, SC_MIN1);
   g2.Cin = x->dM1; g2.sCin = NN; g2.ldcin = x->N; g2.beta = 1.0;
-  launch(x, KC_GEMM, [&] { gemm(g2, st); });
+  stab_gemm(x, g2);
   launch(x, KC_SOLVE, [&] { solve_stab(x->dXs, R.U, R.sU, R.D, R.sD, x->dY, x->dWS, x->N, x->batch(), st); });
   auto g3 = gemm_base<double>(x, L.U, L.sU, x->dY, NN, x->dG);
   g3.brow = vec_scale(L.D, L.sD, SC_INV_MAX1);
@@ -679,7 +689,7 @@ void recompute(nmc_ctx* x, const UDTView& R, const UDTView& L, bool drift) {
   }
   if (x->fp32()) { g3.Cf = x->dGf; g3.sCf = NN; }
   if (x->dfp()) { g3.Cdf = x->dG2; g3.sCdf = NN; }
-  launch(x, KC_GEMM, [&] { gemm(g3, st); });
+  stab_gemm(x, g3);
   if (drift) {
     launch(x, KC_OTHER, [&] {
       fold_drift(x->dDriftStab, x->dDrift, x->dHist, x->hist_cap, x->dCtr + 2, x->chains(), st);
@@ -1001,6 +1011,7 @@ void nmc_default_options(nmc_options* o) {
   o->cuda_stream = nullptr;
   o->ph_symmetric = 0;
   o->sweep_graphs = 1;
+  o->stab_pairs = 0;
 }
 
 // Sites of a lattice, or 0 if the lattice and sizes are not accepted: square needs even
@@ -1061,8 +1072,10 @@ nmc_status nmc_configure(nmc_ctx* x, const nmc_options* o) {
       (n.precision != NMC_FP64 && n.precision != NMC_FP32 && n.precision != NMC_SPLIT_BF16 &&
        n.precision != NMC_FP32X2) ||
       n.chain_offset < 0 || n.n_chains > (1 << 20) || (n.ph_symmetric != 0 && n.ph_symmetric != 1) ||
-      (n.sweep_graphs != 0 && n.sweep_graphs != 1))
+      (n.sweep_graphs != 0 && n.sweep_graphs != 1) || (n.stab_pairs != 0 && n.stab_pairs != 1))
     return fail(x, NMC_EINVAL, "invalid nmc_options");
+  if (n.stab_pairs && n.precision != NMC_SPLIT_BF16 && n.precision != NMC_FP32X2)
+    return fail(x, NMC_EINVAL, "stab_pairs applies to the compensated precisions only");
   x->opt = n;
   clamp_delay(x);
   return alloc_all(x);
@@ -1350,7 +1363,8 @@ nmc_status nmc_checkpoint(nmc_ctx* x, void* buf, size_t* n) {
   char* p = (char*)buf;
   const int64_t h[9] = {(int64_t)kCkptMagic, x->N, x->Lt, C, (int64_t)x->seed, x->sweep_counter,
                         x->phase, x->n_series,
-                        x->opt.precision + 16 * x->opt.ph_symmetric + 256 * x->lattice};
+                        x->opt.precision + 16 * x->opt.ph_symmetric + 256 * x->lattice +
+                        4096 * x->opt.stab_pairs};
   std::memcpy(p, h, hdr);
   p += hdr;
   cudaStream_t st = x->st();
@@ -1380,7 +1394,8 @@ nmc_status nmc_restore(nmc_ctx* x, const void* buf, size_t n) {
   std::memcpy(h, buf, hdr);
   const int C = x->opt.n_chains;
   if ((uint64_t)h[0] != kCkptMagic || h[1] != x->N || h[2] != x->Lt || h[3] != C ||
-      (uint64_t)h[4] != x->seed || h[8] != x->opt.precision + 16 * x->opt.ph_symmetric + 256 * x->lattice)
+      (uint64_t)h[4] != x->seed || h[8] != x->opt.precision + 16 * x->opt.ph_symmetric + 256 * x->lattice +
+                        4096 * x->opt.stab_pairs)
     return fail(x, NMC_EINVAL, "nmc_restore: checkpoint does not match this context");
   const size_t nf = (size_t)C * x->Lt * x->N;
   const long long ns = h[7];

@@ -98,6 +98,9 @@ struct GemmArgs {
 
 void gemm(const GemmArgs<double>& g, cudaStream_t st);
 void gemm(const GemmArgs<float>& g, cudaStream_t st);
+// The same FP64-in, FP64-out product with the sums accumulated in FP32 pairs on the FP32
+// pipe (error-free products and sums, ~2^-44 relative to the sum of |a_ik b_kj|)
+void gemm_pair(const GemmArgs<double>& g, cudaStream_t st);
 
 // Double-float GEMM (compensated FP32 pairs): C[b] = e^{V_c} (A[b] (e^{V_b} B[b])) e^{V_c'}
 // where the optional diagonal factors are field exponentials e^{m lam}, m = sigma *

@@ -105,8 +105,10 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
     // warp 0: pivot (largest remaining norm, lowest index on ties), swap, reflector
     // H_p = I - tau v v^T (v_p = 1) zeroing W[p+1:, p]; the other warps wait at the barrier
     if (warp == 0) {
+      // bi starts at p, so a column of NaN norms (non-finite input) pivots in place instead
+      // of selecting no column: the NaN then reaches the outputs and the drift check
       double best = -1.0;
-      int bi = N;
+      int bi = p;
       for (int c = p + lane; c < N; c += 32)
         if (n1[c] > best) { best = n1[c]; bi = c; }
       warp_argmax(best, bi);
@@ -244,7 +246,7 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
   for (int p = 0; p < N; ++p) {
     if (warp == 0) {
       double best = -1.0;
-      int bi = N;
+      int bi = p;   // NaN entries only: pivot in place (see k_qrp)
       for (int r = p + lane; r < N; r += 32) {
         const double a = fabs(Aug[(long long)r * ld + p]);
         if (a > best) { best = a; bi = r; }

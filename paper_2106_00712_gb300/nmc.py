@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
     _fields_ = [("n_chains", ctypes.c_int), ("delay_k", ctypes.c_int),
                 ("precision", ctypes.c_int), ("drift_tol", ctypes.c_double),
                 ("chain_offset", ctypes.c_longlong), ("cuda_stream", ctypes.c_void_p),
-                ("ph_symmetric", ctypes.c_int), ("sweep_graphs", ctypes.c_int)]
+                ("ph_symmetric", ctypes.c_int), ("sweep_graphs", ctypes.c_int),
+                ("stab_pairs", ctypes.c_int)]
 
 
 class Est(ctypes.Structure):
@@ -423,7 +424,7 @@ class Context:
 
     def __init__(self, Lx, Ly, t, U, beta, dtau, n_wrap, seed=0, n_chains=1, delay_k=16,
                  precision=NMC_FP64, drift_tol=0.0, chain_offset=0, stream=None,
-                 ph_symmetric=0, lattice=NMC_SQUARE, sweep_graphs=1):
+                 ph_symmetric=0, lattice=NMC_SQUARE, sweep_graphs=1, stab_pairs=0):
         self.ctx = nmc_create(Lx, Ly, t, U, beta, dtau, n_wrap, seed, lattice)
         o = nmc_default_options()
         o.n_chains, o.delay_k, o.precision = n_chains, delay_k, precision
@@ -431,6 +432,7 @@ class Context:
         o.cuda_stream = stream
         o.ph_symmetric = int(ph_symmetric)
         o.sweep_graphs = int(sweep_graphs)
+        o.stab_pairs = int(stab_pairs)
         try:
             nmc_configure(self.ctx, o)
         except Exception:

@@ -41,13 +41,13 @@ def _ctx(nmc, model, **kw):
 
 def _compare_run(nmc, model, chains, n_sweeps, measure_from=0, delay_k=16, fields=None,
                  check_chains=None, chain_offset=0, precision=0, g_rel=G_REL, ph=0,
-                 after=None):
+                 after=None, **opts):
     """Run n_sweeps on the GPU and on the oracle for the checked chains; compare the
     field after every sweep (bit-exact), G at the end and the accumulated observables.
     `after(c)`, if given, runs on the context before it closes."""
     check = list(range(chains)) if check_chains is None else check_chains
     with _ctx(nmc, model, n_chains=chains, delay_k=delay_k, chain_offset=chain_offset,
-              drift_tol=1e-3, precision=precision, ph_symmetric=ph) as c:
+              drift_tol=1e-3, precision=precision, ph_symmetric=ph, **opts) as c:
         if fields is None:
             c.generate()
             refs = {ch: Chain(model, initial_fields(model, ch + chain_offset), ch + chain_offset)

@@ -89,6 +89,18 @@ def test_state_errors_without_gpu_work(nmc):
     with pytest.raises(nmc.NmcError) as e:
         nmc.nmc_configure(ctx, bad)
     assert e.value.status == nmc.NMC_EINVAL
+    # FP32-pair stabilization products exist for the compensated precisions only
+    for prec in (nmc.NMC_FP64, nmc.NMC_FP32):
+        bad = nmc.nmc_default_options()
+        bad.precision, bad.stab_pairs = prec, 1
+        with pytest.raises(nmc.NmcError) as e:
+            nmc.nmc_configure(ctx, bad)
+        assert e.value.status == nmc.NMC_EINVAL
+    bad = nmc.nmc_default_options()
+    bad.precision, bad.stab_pairs = nmc.NMC_SPLIT_BF16, 2
+    with pytest.raises(nmc.NmcError) as e:
+        nmc.nmc_configure(ctx, bad)
+    assert e.value.status == nmc.NMC_EINVAL
     nmc.nmc_destroy(ctx)
 
 
