@@ -7,27 +7,28 @@
 // e^{-+dtau K/2}, shared by all chains) and one chain operand X (an FP32-pair matrix of one
 // chain and spin). The kernel forms D = A B^T with A = rows of the chain operand and
 // B = rows of the constant, each row scaled by a power of two 2^-e so that its entries lie
-// in (-1/2, 1/2) and cut into 6 slices c_s, multiples of q_s = 2^{-8(s+1)} with
+// in (-1/2, 1/2) and cut into 7 slices c_s, multiples of q_s = 2^{-8(s+1)} with
 // |c_s| <= 256 q_s, each exact in BF16 (stored pre-scaled, so a slice product c_s d_t
 // carries its own weight):
-//     x 2^-e = sum_s c_s   (hi part: slices 0..5; lo part, |lo| < 2^-25: slices 3..5;
-//                           what is left is below 2^-49).
-// Slice products are exact in FP32. The tensor core accumulates them in four accumulators:
-// the groups g = s + t = 0, 1, 2 each in its own (each group sum is an integer multiple of
-// 2^{-8(g+2)} below 2^24 such units for K <= 340, hence exact), and the groups 3..5
-// together (their rounding is ~2^-24 of a term that is itself ~2^-24 of the product). The
-// 21 slice pairs with s + t <= 5 are issued; the dropped pairs weigh < 2^-48 of the row and
-// column maxima. The epilogue adds the four accumulators in FP32 pairs and scales by
-// 2^{e_row + f_col}.
+//     x 2^-e = sum_s c_s   (hi part: slices 0..6; lo part, |lo| < 2^-25: slices 3..6;
+//                           what is left is below 2^-57).
+// Slice products are exact in FP32. The tensor core accumulates the 28 slice pairs with
+// s + t <= 6 into seven accumulators, one per group g = s + t (groups 0..2 exact for
+// K <= 340, group 3 for K <= 160; the dropped pairs weigh < 2^-56 of the row and column
+// maxima). The epilogue adds groups 4..6 in FP32, then groups 0..3 and that sum in FP32
+// pairs, and scales by 2^{e_row + f_col}.
 //
 // Matrix shapes: all batch x N rows of the chain operand are one long M dimension (the
 // constant is shared), cut into tiles of 128 rows (one tensor-memory lane per row); the
-// output columns are cut into tiles of NT <= 64 (four accumulators x NT columns of tensor
-// memory), K into chunks of KC = 32 (16 for N <= 16). One CTA of 128 threads per (row
-// tile, column tile): every thread slices its row of the chain operand, thread 0 issues the
-// TMA copy of the constant's slices and the MMAs, every thread reads its accumulator lane.
-// Two CTAs share an SM (about 72 KB of operands and 256 tensor-memory columns each), so
-// one's slicing and epilogue overlap the other's MMAs.
+// output columns are cut into tiles of NT <= 64 (seven accumulators x NT columns of tensor
+// memory), K into chunks of KC = 32 (16 for N <= 16). One CTA of 544 threads per (row
+// tile, column tile), one CTA per SM: 16 warps slice the chain operand's rows into two
+// shared-memory stages and later read the accumulators, and one warp issues the TMA copies
+// of the constant's slices and the MMAs. (A persistent variant with separate slicing,
+// MMA and epilogue warps overlapping consecutive tiles, the constant resident in shared
+// memory and two accumulator buffers, measured the same time per launch at N = 64: the
+// kernel is bound by its slicing and combining instructions, not by the order of its
+// phases.)
 //
 // C = Cst X (constant on the left) is computed transposed: C^T = X^T Cst^T, so the rows of
 // the chain operand are the columns of X, and the epilogue writes C^T's rows as C's columns.
@@ -73,16 +74,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Test the phase; while it is incomplete the thread is suspended (it issues nothing) until
+// the phase completes or about kSuspendNs nanoseconds pass, so waiting threads do not take
+// issue slots from the working ones.
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n"
       ".reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       "selp.u32 %0, 1, 0, p;\n"
       "}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
