@@ -35,14 +35,22 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// argmax over lanes: larger value wins, lower index on ties
-__device__ __forceinline__ void warp_argmax(double& v, int& idx) {
+// argmax over lanes: larger key wins, lower index on ties. Keys are the bit patterns of
+// non-negative doubles (|x|, squared norms), which order like the values, so the search
+// runs on the integer pipes instead of the narrow FP64 pipe; a lane with no candidate
+// holds key -1.
+__device__ __forceinline__ void warp_argmax(long long& key, int& idx) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const long long ok = __shfl_xor_sync(0xffffffffu, key, o);
     const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    if (ok > key || (ok == key && oi < idx)) { key = ok; idx = oi; }
   }
+}
+
+// key of a non-negative double (a NaN, with its sign bit cleared, orders above +inf)
+__device__ __forceinline__ long long nonneg_key(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffll;
 }
 
 __host__ __device__ inline size_t qrp_small_bytes(int N) {
@@ -79,6 +87,7 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   else
     W = ws + (long long)b * 2 * NN;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int pw = blockIdx.x & 3;
   const int sub = tid & (kQuad - 1);
   const unsigned qmask = 0xFu << (lane & ~(kQuad - 1));
   const double* Xb = X + (long long)b * NN;
@@ -102,15 +111,17 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
 
   const double tol3z = sqrt(DBL_EPSILON);
   for (int p = 0; p < N; ++p) {
-    // warp 0: pivot (largest remaining norm, lowest index on ties), swap, reflector
-    // H_p = I - tau v v^T (v_p = 1) zeroing W[p+1:, p]; the other warps wait at the barrier
-    if (warp == 0) {
-      // bi starts at p, so a column of NaN norms (non-finite input) pivots in place instead
-      // of selecting no column: the NaN then reaches the outputs and the drift check
-      double best = -1.0;
+    // warp pw: pivot (largest remaining norm, lowest index on ties), swap, reflector
+    // H_p = I - tau v v^T (v_p = 1) zeroing W[p+1:, p]; the other warps wait at the barrier.
+    // pw = blockIdx % 4: the CTAs sharing an SM run this serial FP64 step on different
+    // sub-partitions (warp w issues on sub-partition w % 4) instead of all on the first.
+    if (warp == pw) {
+      long long best = -1;
       int bi = p;
-      for (int c = p + lane; c < N; c += 32)
-        if (n1[c] > best) { best = n1[c]; bi = c; }
+      for (int c = p + lane; c < N; c += 32) {
+        const long long kc = nonneg_key(n1[c]);
+        if (kc > best) { best = kc; bi = c; }
+      }
       warp_argmax(best, bi);
       const int piv = bi;
       if (piv != p) {
@@ -227,6 +238,7 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
         double* __restrict__ ws, int N, int use_smem) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_piv;
+  __shared__ double s_inv;
   const int b = blockIdx.x;
   const long long NN = (long long)N * N;
   const int ld = 2 * N;
@@ -243,16 +255,22 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
     Aug[e] = v;
   }
   __syncthreads();
+  const int pw = blockIdx.x & 3;   // the pivot-search warp (see k_qrp)
   for (int p = 0; p < N; ++p) {
-    if (warp == 0) {
-      double best = -1.0;
-      int bi = p;   // NaN entries only: pivot in place (see k_qrp)
+    if (warp == pw) {
+      long long best = -1;
+      int bi = p;
       for (int r = p + lane; r < N; r += 32) {
-        const double a = fabs(Aug[(long long)r * ld + p]);
-        if (a > best) { best = a; bi = r; }
+        const long long kr = nonneg_key(Aug[(long long)r * ld + p]);   // |entry|
+        if (kr > best) { best = kr; bi = r; }
       }
       warp_argmax(best, bi);
-      if (lane == 0) s_piv = bi;
+      // the pivot's reciprocal, once: a division on every warp would cost the narrow FP64
+      // pipe about as much as the elimination step itself
+      if (lane == 0) {
+        s_piv = bi;
+        s_inv = 1.0 / Aug[(long long)bi * ld + p];
+      }
     }
     __syncthreads();
     const int piv = s_piv;
@@ -264,7 +282,7 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
       }
       __syncthreads();
     }
-    const double inv = 1.0 / Aug[p * ld + p];
+    const double inv = s_inv;
     for (int c = p + 1 + tid; c < ld; c += kSolveThreads) Aug[p * ld + c] *= inv;
     __syncthreads();
     // rows over warps, columns over lanes (32-bit indices)
