@@ -53,12 +53,13 @@ def _measured_peaks_file():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"]))
+        return (float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                float(d.get("hbm_gbs", 6800.0)))
     except Exception:
-        return 1900.0, 1700.0   # the profiling recipe's fallback
+        return 1900.0, 1700.0, 6800.0   # the profiling recipe's fallback
 
 
-BF16_PEAK, BF16_PEAK_SUSTAINED = _measured_peaks_file()
+BF16_PEAK, BF16_PEAK_SUSTAINED, HBM_PEAK_GBS = _measured_peaks_file()
 # DRAM bytes per launch of a kernel, from an ncu capture of the same launch configuration
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of the kernel source at
 # capture time; reported as null once the source has changed.
@@ -115,9 +116,15 @@ def class_rooflines(st, base, ns, acc, peaks, tc):
     out = {}
     if st.get("gemm_tc", (0,))[0]:
         a = rate("gemm_tc", OZ_PRODUCTS * 2.0 * N ** 3 * batch)
+        tr = traffic_of("gemm_tc.cu")
+        hbm = {}
+        if tr:
+            launches, timed, ms = st["gemm_tc"]
+            gbs = tr / (ms / max(timed, 1) * 1e-3) / 1e9
+            hbm = {"hbm_gbs": gbs, "hbm_frac": gbs / HBM_PEAK_GBS}
         out["gemm_tc"] = entry("tensor", TC_KERNEL, a, peaks["bf16"],
                                "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst), of measured",
-                               traffic=traffic_of("gemm_tc.cu"),
+                               traffic=tr, **hbm,
                                algorithmic=f"{OZ_PRODUCTS} BF16 slice products of 2N^3 per "
                                            "FP64-class product",
                                achieved_fp64_class=a / OZ_PRODUCTS)
@@ -146,7 +153,14 @@ def class_rooflines(st, base, ns, acc, peaks, tc):
         extra = {}
         if base == "fp32x2":
             extra["frac_of_pair_ceiling"] = a / (peaks["fp32"] / PAIR_INSTR_PER_FMA)
-            extra["traffic"] = traffic_of("flip.cu")
+            tr = traffic_of("flip.cu")
+            extra["traffic"] = tr
+            if tr:   # DRAM bytes of the captured launch over this run's launch time
+                launches, timed, ms = st["flip"]
+                gbs = tr / (ms / max(timed, 1) * 1e-3) / 1e9
+                extra["hbm_gbs"] = gbs
+                extra["hbm_frac"] = gbs / HBM_PEAK_GBS
+                extra["hbm_peak_source"] = "MEASURED_PEAKS.json hbm_gbs (copy), of measured"
         out["flip"] = entry("alu", kern, a, peaks[simt],
                             f"{simt.upper()} FMA probe (nmc_fma_probe), of measured",
                             algorithmic="per accepted flip and spin 2N^2 + 2Nk (delayed rank-k "

@@ -143,10 +143,15 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
       for (int r = p + 1 + lane; r < N; r += 32) xn2 += col[r] * col[r];
       xn2 = warp_sum(xn2);
       double t = 0.0;
-      if (xn2 > 0.0) {
-        const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-        t = (beta - alpha) / beta;
-        const double scal = 1.0 / (alpha - beta);
+      if (xn2 > 0.0) {   // (xn2 is the same in every lane after the butterfly sum)
+        // the square root and the two divisions on lane 0 only, then broadcast
+        double beta = 0.0, scal = 0.0;
+        if (lane == 0) {
+          beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+          t = (beta - alpha) / beta;
+          scal = 1.0 / (alpha - beta);
+        }
+        scal = __shfl_sync(0xffffffffu, scal, 0);
         for (int r = p + 1 + lane; r < N; r += 32) col[r] *= scal;
         __syncwarp();
         if (lane == 0) col[p] = beta;
