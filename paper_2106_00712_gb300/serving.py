@@ -336,6 +336,45 @@ def serve_stream(n_requests=64, budget_gb=100.0, load=0.7, seed=0, precision=2,
     return out
 
 
+def batched_mix_rate(n_requests=2000, seed=0, chains_per_class=128, warm=2, sweeps=4,
+                     precision=2, **kw):
+    """The batched path on the serving mix, for comparison with the loop's capacity: each
+    (L, beta, U) class of the mix runs alone as one context of `chains_per_class` chains
+    (the largest pool: max_slots x chains), timed over `sweeps` measuring sweeps after
+    `warm` (CUDA events); the mix's rate is its total flips over the time its classes would
+    take at those rates one after another (no overlap between classes)."""
+    import torch
+    from . import nmc
+    nmc.load()
+    reqs = poisson_stream(n_requests, rate=1.0, seed=seed + 1, **kw)
+    classes = {}
+    for r in reqs:
+        c = classes.setdefault((r.L, r.beta, r.U, r.dtau, r.n_wrap), [0, 0.0])
+        c[0] += r.flips
+    stream = torch.cuda.current_stream()
+    per = []
+    total_time = 0.0
+    for (L, beta, U, dtau, n_wrap), (flips, _) in sorted(classes.items()):
+        with nmc.Context(L, L, 1.0, U, beta, dtau, n_wrap, seed=2106, n_chains=chains_per_class,
+                         precision=precision, drift_tol=1e300,
+                         stream=stream.cuda_stream) as c:
+            c.generate()
+            c.sweep(warm, measure=1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.sweep(sweeps, measure=1)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+        rate = chains_per_class * L * L * int(round(beta / dtau)) * sweeps / (ms * 1e-3)
+        total_time += flips / rate
+        per.append({"L": L, "beta": beta, "U": U, "n_wrap": n_wrap, "flips_per_s": rate})
+    flips = sum(r.flips for r in reqs)
+    return {"classes": per, "mix_flips_per_s": flips / total_time,
+            "chains_per_class": chains_per_class, "n_requests": n_requests}
+
+
 def main():
     import argparse
     import json
@@ -348,7 +387,14 @@ def main():
     ap.add_argument("--warm", type=int, default=20)
     ap.add_argument("--meas", type=int, default=50)
     ap.add_argument("--max-slots", type=int, default=8)
+    ap.add_argument("--batched-mix", action="store_true",
+                    help="time the batched path on each class of the mix instead of serving")
     args = ap.parse_args()
+    if args.batched_mix:
+        print(json.dumps(batched_mix_rate(args.requests, chains_per_class=args.max_slots *
+                                          args.chains, chains=args.chains, n_warm=args.warm,
+                                          n_meas=args.meas)))
+        return
     print(json.dumps(serve_stream(args.requests, args.budget_gb, args.load, chains=args.chains,
                                   n_warm=args.warm, n_meas=args.meas, max_slots=args.max_slots,
                                   saturation_requests=args.saturation_requests)))
