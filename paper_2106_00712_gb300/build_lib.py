@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnmc.so")
 SOURCES = ["gemm.cu", "gemm_df.cu", "gemm_tc.cu", "stab.cu", "flip.cu", "misc.cu", "nmc_api.cu", "noalloc.cu",
-           "nimc.cu", "probe.cu", "lattice.cpp"]
+           "nimc.cu", "cgen.cu", "probe.cu", "lattice.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -79,6 +79,11 @@ EXPORTED_GEN = ("nmc_gen_paper_arch", "nmc_gen_create", "nmc_gen_get_params",
                 "nmc_gen_train", "nmc_gen_steps", "nmc_gen_set_clip", "nmc_gen_last_error", "nmc_gen_destroy")
 
 
+EXPORTED_CGEN = ("nmc_cgen_create", "nmc_cgen_n_params", "nmc_cgen_get_params",
+                 "nmc_cgen_set_params", "nmc_cgen_forward", "nmc_cgen_loss_grad",
+                 "nmc_cgen_train_step", "nmc_cgen_sample", "nmc_cgen_destroy")
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_longlong),
                 ("timed", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
@@ -151,6 +156,16 @@ def load():
         "nmc_gen_set_clip": (i, [vp, d]),
         "nmc_gen_last_error": (ctypes.c_char_p, [vp]),
         "nmc_gen_destroy": (None, [vp]),
+        # include/nmc_cgen.h
+        "nmc_cgen_create": (i, [i, i, i, i, ctypes.c_uint64, i, vp, P(vp)]),
+        "nmc_cgen_n_params": (i, [vp, P(ctypes.c_longlong)]),
+        "nmc_cgen_get_params": (i, [vp, vp]),
+        "nmc_cgen_set_params": (i, [vp, vp]),
+        "nmc_cgen_forward": (i, [vp, vp, i, vp]),
+        "nmc_cgen_loss_grad": (i, [vp, vp, vp, i, P(d), vp]),
+        "nmc_cgen_train_step": (i, [vp, vp, i, ctypes.c_longlong, ctypes.c_float, P(d)]),
+        "nmc_cgen_sample": (i, [vp, ctypes.c_longlong, i, vp, vp]),
+        "nmc_cgen_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -541,6 +556,92 @@ def _gcheck(g, status):
     if status != NMC_OK:
         msg = load().nmc_gen_last_error(g) if g else b""
         raise NmcError(status, (msg or b"").decode())
+
+
+class ConvGenerator:
+    """Owning wrapper of an nmc_cgen: four periodic 3D convolutions (1 -> C -> C -> C -> 1
+    channels) from N(0,1) noise to Bernoulli logits per field entry, trained by maximum
+    likelihood (include/nmc_cgen.h). Device-pointer arguments are integers (e.g. torch
+    ``data_ptr()``); arrays of noise, logits and fields are [n][L_tau][Ly][Lx]."""
+
+    def __init__(self, Lx, Ly, L_tau, channels=32, seed=0, max_batch=64, stream=None):
+        h = ctypes.c_void_p()
+        st = load().nmc_cgen_create(Lx, Ly, L_tau, channels, seed, max_batch, stream,
+                                    ctypes.byref(h))
+        if st != NMC_OK:
+            raise NmcError(st, "nmc_cgen_create rejected its arguments")
+        self.g = h
+        self.shape = (L_tau, Ly, Lx)
+        self.C = channels
+        self.max_batch = max_batch
+
+    def _check(self, st, what):
+        if st != NMC_OK:
+            raise NmcError(st, what)
+
+    def n_params(self):
+        n = ctypes.c_longlong(0)
+        self._check(load().nmc_cgen_n_params(self.g, ctypes.byref(n)), "nmc_cgen_n_params")
+        return n.value
+
+    def get_params(self):
+        th = np.empty(self.n_params(), dtype=np.float32)
+        self._check(load().nmc_cgen_get_params(self.g, _ptr(th)), "nmc_cgen_get_params")
+        return th
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        if th.size != self.n_params():
+            raise ValueError("parameter count")
+        self._check(load().nmc_cgen_set_params(self.g, _ptr(th)), "nmc_cgen_set_params")
+
+    def params(self):
+        """[(W, b)] per layer from the flat FP32 array (layouts of include/nmc_cgen.h)."""
+        th = self.get_params().astype(np.float64)
+        C, out, o = self.C, [], 0
+        for ci, co in ((1, C), (C, C), (C, C), (C, 1)):
+            W = th[o:o + co * ci * 27].reshape(co, ci, 3, 3, 3)
+            o += co * ci * 27
+            b = th[o:o + co]
+            o += co
+            out.append((W, b))
+        return out
+
+    def forward(self, d_z, n, d_logits):
+        self._check(load().nmc_cgen_forward(self.g, d_z, n, d_logits), "nmc_cgen_forward")
+
+    def loss_grad(self, d_z, d_fields, n, d_grad):
+        loss = ctypes.c_double(0.0)
+        self._check(load().nmc_cgen_loss_grad(self.g, d_z, d_fields, n, ctypes.byref(loss),
+                                              d_grad), "nmc_cgen_loss_grad")
+        return loss.value
+
+    def train_step(self, d_fields, n, sample0, lr):
+        loss = ctypes.c_double(0.0)
+        self._check(load().nmc_cgen_train_step(self.g, d_fields, n, sample0, lr,
+                                               ctypes.byref(loss)), "nmc_cgen_train_step")
+        return loss.value
+
+    def sample(self, n0, n, d_fields, d_logits=None):
+        self._check(load().nmc_cgen_sample(self.g, n0, n, d_fields, d_logits),
+                    "nmc_cgen_sample")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def close(self):
+        if self.g is not None:
+            load().nmc_cgen_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Generator:

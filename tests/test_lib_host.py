@@ -32,6 +32,23 @@ def test_exports_every_declared_symbol(nmc):
     assert "sm_103a" in nmc.nmc_version()
 
 
+def test_exports_every_conv_generator_symbol(nmc):
+    header = open(os.path.join(ROOT, "include", "nmc_cgen.h")).read()
+    declared = set(re.findall(r"\b(nmc_cgen_[a-z_]+)\s*\(", header))
+    assert declared == set(nmc.EXPORTED_CGEN), declared ^ set(nmc.EXPORTED_CGEN)
+    lib = ctypes.CDLL(nmc.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_conv_generator_rejects_bad_sizes_without_gpu_work(nmc):
+    lib = nmc.load()
+    h = ctypes.c_void_p()
+    for args in ((0, 8, 40, 32), (8, 8, 40, 0), (8, 8, 40, 65), (8, 8, 0, 32)):
+        assert lib.nmc_cgen_create(*args, 0, 4, None, ctypes.byref(h)) == nmc.NMC_EINVAL
+    assert lib.nmc_cgen_create(8, 8, 40, 32, 0, 0, None, ctypes.byref(h)) == nmc.NMC_EINVAL
+
+
 def test_exports_every_generator_symbol(nmc):
     header = open(os.path.join(ROOT, "include", "nmc_gen.h")).read()
     declared = set(re.findall(r"\b(nmc_gen_[a-z_]+)\s*\(", header))
