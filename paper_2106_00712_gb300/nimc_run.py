@@ -29,7 +29,11 @@ bounds each step's gradient norm (clip = 1): single-configuration estimators are
 unbounded, and without a bound one configuration's gradient (norm > 1e19) overflowed
 Adam's second moment and froze the generator.
 
-Usage: python -m paper_2106_00712_gb300.nimc_run [--workload honeycomb|square8]
+"square8-ml" -- the convolutional generator of include/nmc_cgen.h on the same 8x8 lattice,
+trained by maximum likelihood on 20000 DQMC fields (one every 10 sweeps), judged the same way
+(run_ml).
+
+Usage: python -m paper_2106_00712_gb300.nimc_run [--workload honeycomb|square8|square8-ml]
        [--train 1000] [--short 10] [--epochs 15] [--batch 3] [--gen N] [--sweeps 60]
 Prints one JSON object.
 """
@@ -164,9 +168,103 @@ def run(workload="honeycomb", n_train=1000, n_short=10, epochs=15, batch=3, lr=1
     return out
 
 
+def run_ml(n_fields=20000, every=10, warm=100, chains=256, channels=32, epochs=3, batch=64,
+           lr=1e-3, n_gen=4096, sweeps=60, precision=nmc.NMC_FP64, ph=1, seed=2106):
+    """The convolutional generator (include/nmc_cgen.h) on the 8x8 lattice at U = 4, beta = 4
+    (fields of shape L_tau x 8 x 8 = 40 x 8 x 8):
+    1. training fields: `chains` DQMC chains (SPLIT_BF16) from random fields, `warm` sweeps,
+       then one field per chain every `every` sweeps until n_fields are collected;
+    2. maximum-likelihood training (Adam, lr, batches of `batch` fields with fresh noise);
+    3. the judge: n_gen chains from generated fields and n_gen from random fields, per-sweep
+       means of E and D, and the first sweep from which each stays at equilibrium (the
+       reference: a long run of random starts).
+    With noise independent of the fields the likelihood's optimum is a constant logit per
+    entry, the log-odds of its mean occupation (oracle.cgen.optimal_bias), so the judge is
+    expected to find generated starts no better than random ones; the run measures it, with
+    a second set of random starts (another seed) to show how far the convergence sweep moves
+    between two draws of one start distribution."""
+    import torch
+    wl = SQUARE_8x8.with_(n_wrap=5)
+    out = {"workload": "square8-ml", "lattice": f"{wl.lattice} {wl.Lx}x{wl.Ly}", "U": wl.U,
+           "beta": wl.beta, "L_tau": wl.L_tau, "n_fields": n_fields, "every": every,
+           "warm": warm, "chains": chains, "channels": channels, "epochs": epochs,
+           "batch": batch, "lr": lr, "n_gen": n_gen, "sweeps": sweeps}
+    t0 = time.perf_counter()
+    fields = []
+    with _ctx(wl, chains, seed + 11, nmc.NMC_SPLIT_BF16, 0) as c:
+        c.generate()
+        c.sweep(warm, measure=0)
+        while sum(len(f) for f in fields) < n_fields:
+            c.sweep(every, measure=0)
+            fields.append(c.fields())
+    data = np.concatenate(fields)[:n_fields]                  # [n][L_tau][N], +-1
+    out["data_mean_occupation"] = float(((1 + data) / 2).mean())
+    out["t_fields_s"] = time.perf_counter() - t0
+    _log(out, "data_mean_occupation", "t_fields_s")
+    t1 = time.perf_counter()
+    rng = np.random.default_rng(seed)
+    gen = nmc.ConvGenerator(wl.Lx, wl.Ly, wl.L_tau, channels=channels, seed=seed,
+                            max_batch=batch)
+    d_data = torch.from_numpy(data.astype(np.int8)).cuda()
+    epoch_loss, sample = [], 0
+    for _ in range(epochs):
+        order = torch.from_numpy(rng.permutation(n_fields)).cuda()
+        tot, cnt = 0.0, 0
+        for k in range(0, n_fields - batch + 1, batch):
+            xb = d_data[order[k:k + batch]].contiguous()
+            tot += gen.train_step(xb.data_ptr(), batch, sample, lr)
+            sample += batch
+            cnt += 1
+        epoch_loss.append(tot / cnt)
+    out["epoch_loss"] = epoch_loss
+    y = out["data_mean_occupation"]
+    out["loss_at_ml_optimum"] = float(-(y * np.log(y) + (1 - y) * np.log(1 - y)))
+    out["t_train_s"] = time.perf_counter() - t1
+    _log(out, "epoch_loss", "loss_at_ml_optimum", "t_train_s")
+    # generated fields
+    d_gen = torch.empty((n_gen, wl.L_tau, wl.N), dtype=torch.int8, device="cuda")
+    d_log = torch.empty((batch, wl.L_tau, wl.N), dtype=torch.float32, device="cuda")
+    lstats = []
+    for k in range(0, n_gen, batch):
+        m = min(batch, n_gen - k)
+        gen.sample(k, m, d_gen[k:k + m].data_ptr(), d_log.data_ptr())
+        lstats.append(d_log[:m].double().cpu().numpy())
+    lg = np.concatenate(lstats)
+    out["generated"] = {"mean_occupation": float(((1 + d_gen.double()) / 2).mean().item()),
+                        "logit_mean": float(lg.mean()), "logit_std_over_noise": float(
+                            lg.std(axis=0).mean()), "logit_std_over_entries": float(
+                            lg.mean(axis=0).std())}
+    gen.close()
+    _log(out, "generated")
+    t2 = time.perf_counter()
+    ref = _reference(wl, seed + 5, precision, ph)
+    out["reference"] = ref
+    torch.cuda.synchronize()
+    curves = {}
+    with _ctx(wl, n_gen, seed + 2, precision, ph) as c:
+        nmc.nmc_set_fields_device(c.ctx, d_gen.data_ptr(), d_gen.numel())
+        curves["generated"] = _curve(c, sweeps)
+    with _ctx(wl, n_gen, seed + 3, precision, ph) as c:
+        c.generate()
+        curves["random"] = _curve(c, sweeps)
+    # a second, independent set of random starts: the spread of the convergence sweep
+    # between two draws of the same start distribution
+    with _ctx(wl, n_gen, seed + 4, precision, ph) as c:
+        c.generate()
+        curves["random_2"] = _curve(c, sweeps)
+    out["t_chains_s"] = time.perf_counter() - t2
+    out["converged_at_sweep"] = {
+        k: {key: _converged_at(v, key, ref[key]) for key in ("energy", "double_occ")}
+        for k, v in curves.items()}
+    out["first_sweep"] = {k: {key: v[key][0] for key in ("energy", "double_occ")}
+                          for k, v in curves.items()}
+    out["curves"] = curves
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="honeycomb", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="honeycomb", choices=sorted(WORKLOADS) + ["square8-ml"])
     ap.add_argument("--train", type=int, default=1000)
     ap.add_argument("--short", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=15)
@@ -174,7 +272,11 @@ def main():
     ap.add_argument("--gen", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=60)
     ap.add_argument("--clip", type=float, default=1.0)
+    ap.add_argument("--epochs-ml", type=int, default=3)
     a = ap.parse_args()
+    if a.workload == "square8-ml":
+        print(json.dumps(run_ml(epochs=a.epochs_ml, n_gen=a.gen or 4096, sweeps=a.sweeps)))
+        return
     print(json.dumps(run(a.workload, a.train, a.short, a.epochs, a.batch, n_gen=a.gen,
                          sweeps=a.sweeps, clip=a.clip)))
 
