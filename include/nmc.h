@@ -351,6 +351,15 @@ nmc_status nmc_debug_product(int precision, int N, int batch, int const_is_a, co
 
 const char* nmc_last_error(const nmc_ctx* ctx);
 const char* nmc_version(void);
+
+/* The bounds-checked build (libnmc_debug.so, compiled with NMC_DEBUG): its kernels check
+ * their key indices (pivot rows, panel slots, tile offsets, output entries, chain lists)
+ * and, on a failed check, skip the access and record the check's id; the calls that run
+ * kernels then return NMC_ECUDA naming it. nmc_debug_build: 1 in that build, 0 otherwise.
+ * nmc_debug_checks: the first failed check's id since the library was loaded (0: none;
+ * always 0 outside that build). Host only, synchronous. */
+int nmc_debug_build(void);
+unsigned int nmc_debug_checks(void);
 void nmc_destroy(nmc_ctx* ctx);
 
 #ifdef __cplusplus

@@ -33,23 +33,31 @@ def _deps():
     return files
 
 
-def needs_build():
-    if not os.path.exists(LIB):
+LIB_DEBUG = os.path.join(HERE, "libnmc_debug.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+
+
+def needs_build(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile libnmc.so (returns its path). Raises RuntimeError on a compiler error."""
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra=(), debug=False):
+    """Compile libnmc.so (returns its path); debug=True: the bounds-checked
+    libnmc_debug.so (NMC_DEBUG) instead. Raises RuntimeError on a compiler error."""
+    lib, bdir = (LIB_DEBUG, BUILD_DEBUG) if debug else (LIB, BUILD)
+    if debug:
+        extra = list(extra) + ["-DNMC_DEBUG"]
+    if not force and not needs_build(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + ARCH + NVCC_FLAGS + list(extra)
         if src.endswith(".cpp"):
             cmd += ["-x", "c++"]
@@ -66,16 +74,17 @@ def build(force=False, verbose=False, extra=()):
             sys.stderr.write(f"[{src}]\n{text}\n")
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     link = [nvcc, "-shared", "-o", tmp] + objs + ARCH
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     verbose = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
-    print(build(force=True, verbose=verbose or bool(extra), extra=extra))
+    print(build(force=True, verbose=verbose or bool(extra), extra=extra,
+                debug="--debug" in sys.argv))

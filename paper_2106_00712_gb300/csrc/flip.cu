@@ -19,6 +19,8 @@ namespace nmc {
 
 namespace {
 
+NMC_DEBUG_FLAG
+
 constexpr int kThreads = 256;
 // compensated kernel: 256 threads for the panel entries (one entry of G^'s column or row each
 // at N = 64) plus one warp whose first thread evaluates the ratio meanwhile
@@ -151,11 +153,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_flip(const FlipArgs<T> f) {
         if (kind == 0) {  // column i of G^: a_m = coef (e_i - G^_{:,i})
           T v = Gsp[(long long)r * N + i];
           for (int q = 0; q < m; ++q) v = fma(A_[q * N + r], B_[q * N + i], v);
-          Ap[(sp * KK + m) * N + r] = (sp ? coef1 : coef0) * ((r == i ? T(1) : T(0)) - v);
+          if (NMC_DCHECK(m < KK && sp < ns && r < N, 111))
+            Ap[(sp * KK + m) * N + r] = (sp ? coef1 : coef0) * ((r == i ? T(1) : T(0)) - v);
         } else {          // row i of G^: b_m = G^_{i,:}
           T v = Gsp[(long long)i * N + r];
           for (int q = 0; q < m; ++q) v = fma(A_[q * N + i], B_[q * N + r], v);
-          Bp[(sp * KK + m) * N + r] = v;
+          if (NMC_DCHECK(m < KK && sp < ns && r < N, 112)) Bp[(sp * KK + m) * N + r] = v;
         }
       }
       ++m;
@@ -445,11 +448,12 @@ __global__ void __launch_bounds__(kThreadsDf, 2) k_flip_df(const FlipArgs<df2> f
         for (int q = 0; q < m; ++q) df_fma_acc(ca, A_[q * N + r], B_[q * N + i]);
         df2 v = df_neg(df_finish(ca));
         if (r == i) v = df_add(v, one);
-        Ap[(sp * KK + m) * N + r] = v;          // times the coefficient once accepted
+        if (NMC_DCHECK(m < KK && sp < ns && r < N, 101))
+          Ap[(sp * KK + m) * N + r] = v;        // times the coefficient once accepted
       } else {           // row i of G^, column r
         df2 rb = Gsp[(long long)i * N + r];
         for (int q = 0; q < m; ++q) df_fma_acc(rb, A_[q * N + i], B_[q * N + r]);
-        Bp[(sp * KK + m) * N + r] = df_finish(rb);
+        if (NMC_DCHECK(m < KK && sp < ns && r < N, 102)) Bp[(sp * KK + m) * N + r] = df_finish(rb);
       }
     }
     if (threadIdx.x == rt) {
@@ -496,6 +500,7 @@ __global__ void __launch_bounds__(kThreadsDf, 2) k_flip_df(const FlipArgs<df2> f
       for (int t = threadIdx.x; t < ns * N; t += blockDim.x) {
         const int sp = t / N, r = t % N;
         const long long o = (long long)(sp * KK + m) * N + r;
+        if (!NMC_DCHECK(m < KK, 103)) continue;
         const df2 a = df_mul(s_coef[sp], Ap[o]);
         Ap[o] = a;
         dg[t] = df_add(dg[t], df_mul(a, Bp[o]));
@@ -563,5 +568,7 @@ void flip_slice<df2>(const FlipArgs<df2>& f, int n_chains, cudaStream_t st) {
     k_flip_df<false><<<n_chains, kThreadsDf, bytes, st>>>(f);
   }
 }
+
+NMC_DEBUG_READER(debug_fail_flip)
 
 }  // namespace nmc

@@ -17,6 +17,8 @@ namespace nmc {
 
 namespace {
 
+NMC_DEBUG_FLAG
+
 __device__ __forceinline__ double nan_max(double a, double b) {
   // max that propagates NaN (fmax would drop it)
   return (b > a || b != b) ? b : a;
@@ -59,6 +61,7 @@ __device__ __forceinline__ double brow_at(const TileScales<BM, BN>& sc, const Ge
 template <typename T>
 __device__ __forceinline__ void store_c(const GemmArgs<T>& g, int b, int gm, int gn, double rs,
                                         double cs, double v, double& dmax) {
+  if (!NMC_DCHECK(gm >= 0 && gm < g.M && gn >= 0 && gn < g.N, 401)) return;
   if (g.crow.kind != SC_NONE || g.ccol.kind != SC_NONE) v = v * rs * cs;
   if (g.Cin) v += g.beta * (double)g.Cin[(long long)b * g.sCin + (long long)gm * g.ldcin + gn];
   const T out = (T)v;
@@ -278,5 +281,7 @@ void launch_pair(const GemmArgs<double>& g, cudaStream_t st) {
 void gemm(const GemmArgs<double>& g, cudaStream_t st) { launch(g, st); }
 void gemm_pair(const GemmArgs<double>& g, cudaStream_t st) { launch_pair(g, st); }
 void gemm(const GemmArgs<float>& g, cudaStream_t st) { launch(g, st); }
+
+NMC_DEBUG_READER(debug_fail_gemm)
 
 }  // namespace nmc

@@ -43,6 +43,8 @@ namespace nmc {
 
 namespace {
 
+NMC_DEBUG_FLAG
+
 constexpr int kS = 7;            // slices per operand
 constexpr int kLoFirst = 3;      // first slice of the lo part of an FP32 pair
 constexpr int kAcc = kS;         // one accumulator per group g = s + t = 0..6
@@ -448,8 +450,9 @@ __global__ void __launch_bounds__(SL + 32, SL == 512 ? 1 : 2)
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = df2{v[j].hi * xs, v[j].lo * xs};
-        slice8_store(v, As(st) + (r >> 3) * (KC / 8) * 128 + kp * 128 + (r & 7) * 16,
-                     kM * KC * 2);
+        const int off = (r >> 3) * (KC / 8) * 128 + kp * 128 + (r & 7) * 16;
+        if (NMC_DCHECK(off + 16 <= kM * KC * 2 && r < kM, 301))
+          slice8_store(v, As(st) + off, kM * KC * 2);
       }
       fence_proxy_async();   // the slices, written by threads, are read by the tensor core
       __syncwarp();
@@ -483,6 +486,7 @@ __global__ void __launch_bounds__(SL + 32, SL == 512 ? 1 : 2)
         for (int q = 0; q < kAcc; ++q) tmem_ld8(lane_addr + (uint32_t)(q * NT + c0 + h), a[q]);
         tmem_wait_ld();
         if (!valid_e || !ok) continue;
+        if (!NMC_DCHECK((kAcc - 1) * NT + c0 + h + 8 <= (int)tmem_cols && be < g.batch, 302)) continue;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int n = n_tile * NT + c0 + h + j;
@@ -648,5 +652,7 @@ void gemm_tc(const DfGemmArgs& g, bool const_is_a, const void* tmap, int* err,
   if (const_is_a) run(k_gemm_tc<true, 512>, 512 + 32);
   else run(k_gemm_tc<false, 512>, 512 + 32);
 }
+
+NMC_DEBUG_READER(debug_fail_gemm_tc)
 
 }  // namespace nmc

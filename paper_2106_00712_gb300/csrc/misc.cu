@@ -10,6 +10,8 @@ namespace nmc {
 
 namespace {
 
+NMC_DEBUG_FLAG
+
 __global__ void k_init_fields(int8_t* s, int n_chains, int L, int N, uint32_t k0, uint32_t k1,
                               long long chain_offset) {
   const long long total = (long long)n_chains * L * N;
@@ -36,13 +38,14 @@ __global__ void k_init_fields_list(int8_t* s, int L, int N, uint32_t k0, uint32_
   }
 }
 
-__global__ void k_restart_chain_state(const int* list, const long long* ids, int n,
+__global__ void k_restart_chain_state(const int* list, const long long* ids, int n, int n_chains,
                                       long long sweep, long long* chain_id,
                                       long long* sweep_base, double* sign,
                                       unsigned long long* counts, unsigned long long* drift) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int c = list[j];
+  if (!NMC_DCHECK(c >= 0 && c < n_chains, 501)) return;
   chain_id[c] = ids[j];
   sweep_base[c] = sweep;
   sign[c] = 1.0;
@@ -259,12 +262,12 @@ void init_fields_list(int8_t* s, int L, int N, uint32_t k0, uint32_t k1, const i
                                                                      ids, n);
 }
 
-void restart_chain_state(const int* list, const long long* ids, int n, long long sweep,
+void restart_chain_state(const int* list, const long long* ids, int n, int n_chains, long long sweep,
                          long long* chain_id, long long* sweep_base, double* sign,
                          unsigned long long* counts, unsigned long long* drift,
                          cudaStream_t st) {
   if (n <= 0) return;
-  k_restart_chain_state<<<(n + 127) / 128, 128, 0, st>>>(list, ids, n, sweep, chain_id,
+  k_restart_chain_state<<<(n + 127) / 128, 128, 0, st>>>(list, ids, n, n_chains, sweep, chain_id,
                                                          sweep_base, sign, counts, drift);
 }
 
@@ -318,5 +321,7 @@ void measure(const double* Gt, const double* K, const double* sign, int N, int L
   k_measure<<<n_chains, kMeasThreads, 0, st>>>(Gt, K, sign, N, Lx, lattice, U, ns, acc,
                                                series_idx);
 }
+
+NMC_DEBUG_READER(debug_fail_misc)
 
 }  // namespace nmc

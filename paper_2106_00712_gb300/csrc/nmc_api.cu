@@ -831,7 +831,21 @@ nmc_status ensure_series(nmc_ctx* x, long long need) {
   return NMC_OK;
 }
 
+// first failed index check of the NMC_DEBUG build (0: none, or not a debug build)
+unsigned int debug_failed() {
+  unsigned int (*const readers[])() = {debug_fail_flip, debug_fail_stab, debug_fail_gemm,
+                                       debug_fail_gemm_tc, debug_fail_misc};
+  for (auto r : readers)
+    if (const unsigned int id = r()) return id;
+  return 0u;
+}
+
 nmc_status check_drift(nmc_ctx* x) {
+  if (const unsigned int id = debug_failed()) {
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "index check %u failed (bounds-checked build)", id);
+    return fail(x, NMC_ECUDA, buf);
+  }
   std::vector<unsigned long long> bits(x->chains());
   int err = 0;
   NMC_CUDA(x, cudaMemcpyAsync(bits.data(), x->dDrift, bits.size() * sizeof(unsigned long long),
@@ -1530,7 +1544,8 @@ nmc_status nmc_restart_chains(nmc_ctx* x, const int* chains, const long long* gl
                        (uint32_t)(x->seed >> 32), x->dList, x->dIds, n, st);
     });
     launch(x, KC_OTHER, [&] {
-      restart_chain_state(x->dList, x->dIds, n, x->sweep_counter, x->dChainId, x->dSweepBase,
+      restart_chain_state(x->dList, x->dIds, n, x->chains(), x->sweep_counter, x->dChainId,
+                          x->dSweepBase,
                           x->dSign, x->dCounts, x->dDrift, st);
     });
   }
@@ -1657,6 +1672,16 @@ nmc_status nmc_graph_stats(const nmc_ctx* x, long long* recorded, long long* rep
 const char* nmc_last_error(const nmc_ctx* x) { return x ? x->err.c_str() : "null context"; }
 
 const char* nmc_version(void) { return "libnmc 0.1 (sm_103a)"; }
+
+int nmc_debug_build(void) {
+#ifdef NMC_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+unsigned int nmc_debug_checks(void) { return debug_failed(); }
 
 void nmc_destroy(nmc_ctx* x) {
   if (!x) return;

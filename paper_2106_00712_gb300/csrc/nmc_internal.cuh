@@ -21,6 +21,37 @@ constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
 constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+// Index checks of the NMC_DEBUG build (a bounds-checked variant of the library, built
+// beside it as libnmc_debug.so): a failed check records its id in its translation unit's
+// device flag (the first failure wins) and the kernel skips the guarded access; the
+// library reads the flags after each call that runs kernels. Without NMC_DEBUG a check is
+// the constant true and the flags do not exist.
+#ifdef NMC_DEBUG
+#define NMC_DEBUG_FLAG static __device__ unsigned int g_dbg_fail = 0u;
+#define NMC_DCHECK(cond, id) \
+  ((cond) ? true : (atomicCAS(&g_dbg_fail, 0u, (unsigned int)(id)), false))
+#define NMC_DEBUG_READER(fn)                                     \
+  unsigned int fn() {                                            \
+    unsigned int v = 0u;                                         \
+    if (cudaMemcpyFromSymbol(&v, g_dbg_fail, sizeof v) != cudaSuccess) { \
+      cudaGetLastError();                                        \
+      return 0xffffffffu;                                        \
+    }                                                            \
+    return v;                                                    \
+  }
+#else
+#define NMC_DEBUG_FLAG
+#define NMC_DCHECK(cond, id) true
+#define NMC_DEBUG_READER(fn) \
+  unsigned int fn() { return 0u; }
+#endif
+// the first failed check id of each translation unit with checks (0: none)
+unsigned int debug_fail_flip();
+unsigned int debug_fail_stab();
+unsigned int debug_fail_gemm();
+unsigned int debug_fail_gemm_tc();
+unsigned int debug_fail_misc();
+
 constexpr uint32_t kTagFlip = 0u;
 constexpr uint32_t kTagInit = 1u;
 
@@ -190,7 +221,7 @@ void init_fields_list(int8_t* s, int L, int N, uint32_t k0, uint32_t k1, const i
                       const long long* ids, int n, cudaStream_t st);
 // Start the listed chains afresh: chain_id = ids, sweep_base = sweep, sign = +1, counts and
 // drift cleared (device arrays of n entries; sign/counts/drift indexed by chain).
-void restart_chain_state(const int* list, const long long* ids, int n, long long sweep,
+void restart_chain_state(const int* list, const long long* ids, int n, int n_chains, long long sweep,
                          long long* chain_id, long long* sweep_base, double* sign,
                          unsigned long long* counts, unsigned long long* drift,
                          cudaStream_t st);

@@ -21,6 +21,8 @@ namespace nmc {
 
 namespace {
 
+NMC_DEBUG_FLAG
+
 constexpr int kThreads = 256;
 // Gauss-Jordan: 16 warps (rows over warps, columns over lanes), so a matrix alone on an SM
 // (the tail of a batch that does not fill the GPU in one wave) still has the warps to hide
@@ -123,7 +125,7 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
         if (kc > best) { best = kc; bi = c; }
       }
       warp_argmax(best, bi);
-      const int piv = bi;
+      const int piv = NMC_DCHECK(bi >= p && bi < N, 201) ? bi : p;
       if (piv != p) {
         for (int r = lane; r < N; r += 32) {
           const double t0 = W[(long long)p * N + r];
@@ -273,6 +275,7 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
       // the pivot's reciprocal, once: a division on every warp would cost the narrow FP64
       // pipe about as much as the elimination step itself
       if (lane == 0) {
+        if (!NMC_DCHECK(bi >= p && bi < N, 202)) bi = p;
         s_piv = bi;
         s_inv = 1.0 / Aug[(long long)bi * ld + p];
       }
@@ -330,5 +333,7 @@ bool stab_needs_workspace(int N) {
   const size_t small = (qrp_small_bytes(N) + 15) & ~(size_t)15;
   return small + 2 * (size_t)N * N * sizeof(double) > kSmemLimit;
 }
+
+NMC_DEBUG_READER(debug_fail_stab)
 
 }  // namespace nmc

@@ -11,7 +11,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libnmc.so")
+# the library this binding loads: the in-tree build, or another build of the same ABI named
+# by NMC_LIB_PATH (e.g. the bounds-checked libnmc_debug.so)
+LIB_PATH = os.environ.get("NMC_LIB_PATH") or os.path.join(HERE, "libnmc.so")
 
 NMC_OK, NMC_EINVAL, NMC_ENOMEM, NMC_ECUDA, NMC_ENUMERIC, NMC_ETIMEOUT, NMC_ESTATE = range(7)
 STATUS_NAMES = {0: "NMC_OK", 1: "NMC_EINVAL", 2: "NMC_ENOMEM", 3: "NMC_ECUDA",
@@ -30,7 +32,7 @@ EXPORTED = ("nmc_create", "nmc_configure", "nmc_default_options", "nmc_set_field
             "nmc_green_noalloc", "nmc_debug_fail_alloc", "nmc_fma_probe", "nmc_debug_product",
             "nmc_restart_chains", "nmc_series_range",
             "nmc_last_error",
-            "nmc_version", "nmc_destroy")
+            "nmc_version", "nmc_destroy", "nmc_debug_build", "nmc_debug_checks")
 
 
 class NmcError(RuntimeError):
@@ -138,6 +140,8 @@ def load():
         "nmc_debug_product": (i, [i, i, i, i, vp, vp, vp, i, i, i, i, d, vp, vp]),
         "nmc_last_error": (ctypes.c_char_p, [vp]),
         "nmc_version": (ctypes.c_char_p, []),
+        "nmc_debug_build": (i, []),
+        "nmc_debug_checks": (ctypes.c_uint, []),
         "nmc_destroy": (None, [vp]),
         # include/nmc_gen.h
         "nmc_gen_paper_arch": (None, [P(GenArch)]),
