@@ -434,27 +434,58 @@ __global__ void __launch_bounds__(kThreadsDf, 2) k_flip_df(const FlipArgs<df2> f
   // are double-buffered by attempt parity (see k_flip).
   const df2 one{1.f, 0.f};
   const int rt = kPanelThreads;   // the ratio thread: lane 0 of the last warp
+  // entry t of the panels (kind 0: column i of G^, kind 1: row i; spin sp; index r)
+  auto panel_entry = [&](int t, int i, int m) {
+    const int kind = t / (ns * N), e = t - kind * ns * N;
+    const int sp = e / N, r = e % N;
+    const df2* Gsp = G + sp * NN;
+    const df2* A_ = Ap + sp * KK * N;
+    const df2* B_ = Bp + sp * KK * N;
+    if (kind == 0) {   // column i of G^, row r
+      df2 ca = Gsp[(long long)r * N + i];
+      for (int q = 0; q < m; ++q) df_fma_acc(ca, A_[q * N + r], B_[q * N + i]);
+      df2 v = df_neg(df_finish(ca));
+      if (r == i) v = df_add(v, one);
+      if (NMC_DCHECK(m < KK && sp < ns && r < N, 101))
+        Ap[(sp * KK + m) * N + r] = v;        // times the coefficient once accepted
+    } else {           // row i of G^, column r
+      df2 rb = Gsp[(long long)i * N + r];
+      for (int q = 0; q < m; ++q) df_fma_acc(rb, A_[q * N + i], B_[q * N + r]);
+      if (NMC_DCHECK(m < KK && sp < ns && r < N, 102)) Bp[(sp * KK + m) * N + r] = df_finish(rb);
+    }
+  };
+  // When one pass of the panel threads covers both panels (2 ns N <= 256, so N <= 64), each
+  // thread keeps one entry for the whole slice: its column or row, spin and index are
+  // computed once here instead of by integer divisions at every attempt.
+  const bool one_pass = 2 * ns * N <= kPanelThreads;
+  const int tp = threadIdx.x;
+  const bool has_entry = tp < 2 * ns * N && tp < kPanelThreads;
+  const int p_kind = has_entry ? tp / (ns * N) : 0;
+  const int p_e = tp - p_kind * ns * N;
+  const int p_sp = has_entry ? p_e / N : 0, p_r = has_entry ? p_e % N : 0;
+  const df2* const pG = G + p_sp * NN;
+  const df2* const pA = Ap + p_sp * KK * N;
+  const df2* const pB = Bp + p_sp * KK * N;
+  df2* const pOut = (p_kind == 0 ? Ap : Bp) + p_sp * KK * N + p_r;   // + m N
   int m = 0;
   for (int i = 0; i < N; ++i) {
-    for (int t = threadIdx.x; t < 2 * ns * N && threadIdx.x < kPanelThreads;
-         t += kPanelThreads) {
-      const int kind = t / (ns * N), e = t - kind * ns * N;
-      const int sp = e / N, r = e % N;
-      const df2* Gsp = G + sp * NN;
-      const df2* A_ = Ap + sp * KK * N;
-      const df2* B_ = Bp + sp * KK * N;
-      if (kind == 0) {   // column i of G^, row r
-        df2 ca = Gsp[(long long)r * N + i];
-        for (int q = 0; q < m; ++q) df_fma_acc(ca, A_[q * N + r], B_[q * N + i]);
-        df2 v = df_neg(df_finish(ca));
-        if (r == i) v = df_add(v, one);
-        if (NMC_DCHECK(m < KK && sp < ns && r < N, 101))
-          Ap[(sp * KK + m) * N + r] = v;        // times the coefficient once accepted
-      } else {           // row i of G^, column r
-        df2 rb = Gsp[(long long)i * N + r];
-        for (int q = 0; q < m; ++q) df_fma_acc(rb, A_[q * N + i], B_[q * N + r]);
-        if (NMC_DCHECK(m < KK && sp < ns && r < N, 102)) Bp[(sp * KK + m) * N + r] = df_finish(rb);
+    if (one_pass) {
+      if (has_entry) {
+        // the same operations as panel_entry, on this thread's fixed entry
+        if (p_kind == 0) {   // column i of G^, row p_r
+          df2 ca = pG[(long long)p_r * N + i];
+          for (int q = 0; q < m; ++q) df_fma_acc(ca, pA[q * N + p_r], pB[q * N + i]);
+          df2 v = df_neg(df_finish(ca));
+          if (p_r == i) v = df_add(v, one);
+          if (NMC_DCHECK(m < KK, 104)) pOut[m * N] = v;
+        } else {             // row i of G^, column p_r
+          df2 rb = pG[(long long)i * N + p_r];
+          for (int q = 0; q < m; ++q) df_fma_acc(rb, pA[q * N + i], pB[q * N + p_r]);
+          if (NMC_DCHECK(m < KK, 105)) pOut[m * N] = df_finish(rb);
+        }
       }
+    } else if (threadIdx.x < kPanelThreads) {
+      for (int t = threadIdx.x; t < 2 * ns * N; t += kPanelThreads) panel_entry(t, i, m);
     }
     if (threadIdx.x == rt) {
       const int s = sl[i];
@@ -497,13 +528,23 @@ __global__ void __launch_bounds__(kThreadsDf, 2) k_flip_df(const FlipArgs<df2> f
     }
     __syncthreads();
     if (s_accept[i & 1]) {
-      for (int t = threadIdx.x; t < ns * N; t += blockDim.x) {
-        const int sp = t / N, r = t % N;
-        const long long o = (long long)(sp * KK + m) * N + r;
-        if (!NMC_DCHECK(m < KK, 103)) continue;
-        const df2 a = df_mul(s_coef[sp], Ap[o]);
-        Ap[o] = a;
-        dg[t] = df_add(dg[t], df_mul(a, Bp[o]));
+      if (one_pass) {   // thread t < ns N: spin t / N, index t % N (ns N <= 128 <= threads)
+        if (tp < ns * N && NMC_DCHECK(m < KK, 103)) {
+          const int sp = tp >= N ? 1 : 0, r = tp - sp * N;
+          const long long o = (long long)(sp * KK + m) * N + r;
+          const df2 a = df_mul(s_coef[sp], Ap[o]);
+          Ap[o] = a;
+          dg[tp] = df_add(dg[tp], df_mul(a, Bp[o]));
+        }
+      } else {
+        for (int t = threadIdx.x; t < ns * N; t += blockDim.x) {
+          const int sp = t / N, r = t % N;
+          const long long o = (long long)(sp * KK + m) * N + r;
+          if (!NMC_DCHECK(m < KK, 103)) continue;
+          const df2 a = df_mul(s_coef[sp], Ap[o]);
+          Ap[o] = a;
+          dg[t] = df_add(dg[t], df_mul(a, Bp[o]));
+        }
       }
       ++m;
       __syncthreads();
