@@ -83,7 +83,10 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   double* n2 = n1 + N;
   double* tau = n2 + N;
   int* perm = (int*)(tau + N);
-  double* W;  // column-major: W[c*N + r]; becomes Q at the end
+  // column-major with leading dimension N + 1 (W[c*ldw + r]): the 32 columns of a warp fall
+  // on different banks when each thread walks its own column; W becomes Q at the end
+  const int ldw = N + 1;
+  double* W;
   if (use_smem)
     W = (double*)(smraw + ((qrp_small_bytes(N) + 15) & ~(size_t)15));
   else
@@ -96,7 +99,7 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
 
   for (int e = tid; e < (int)NN; e += kThreads) {
     const int r = e / N, c = e - r * N;
-    W[c * N + r] = Xb[e];
+    W[(long long)c * ldw + r] = Xb[e];
   }
   for (int c = tid; c < N; c += kThreads) perm[c] = c;
   __syncthreads();
@@ -104,7 +107,7 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
     const int c = c0 + tid / kQuad;
     if (c < N) {
       double s = 0.0;
-      for (int r = sub; r < N; r += kQuad) { const double v = W[(long long)c * N + r]; s += v * v; }
+      for (int r = sub; r < N; r += kQuad) { const double v = W[(long long)c * ldw + r]; s += v * v; }
       s = quad_sum(s, qmask);
       if (sub == 0) { n1[c] = s; n2[c] = s; }
     }
@@ -128,9 +131,9 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
       const int piv = NMC_DCHECK(bi >= p && bi < N, 201) ? bi : p;
       if (piv != p) {
         for (int r = lane; r < N; r += 32) {
-          const double t0 = W[(long long)p * N + r];
-          W[(long long)p * N + r] = W[(long long)piv * N + r];
-          W[(long long)piv * N + r] = t0;
+          const double t0 = W[(long long)p * ldw + r];
+          W[(long long)p * ldw + r] = W[(long long)piv * ldw + r];
+          W[(long long)piv * ldw + r] = t0;
         }
         if (lane == 0) {
           double t1 = n1[p]; n1[p] = n1[piv]; n1[piv] = t1;
@@ -139,7 +142,7 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
         }
       }
       __syncwarp();
-      double* col = W + (long long)p * N;
+      double* col = W + (long long)p * ldw;
       const double alpha = col[p];
       double xn2 = 0.0;
       for (int r = p + 1 + lane; r < N; r += 32) xn2 += col[r] * col[r];
@@ -162,33 +165,31 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
     }
     __syncthreads();
     const double tp = tau[p];
-    const double* v = W + (long long)p * N;
-    for (int c0 = p + 1; c0 < N; c0 += kColsPerPass) {
-      const int c = c0 + tid / kQuad;
-      if (c < N) {
-        double* col = W + (long long)c * N;
-        double rp = col[p];
-        if (tp != 0.0) {
-          double dot = 0.0;
-          for (int r = p + 1 + sub; r < N; r += kQuad) dot += v[r] * col[r];
-          dot = quad_sum(dot, qmask) + rp;
-          const double f = tp * dot;
-          for (int r = p + 1 + sub; r < N; r += kQuad) col[r] -= f * v[r];
-          rp -= f;
-          __syncwarp(qmask);
-          if (sub == 0) col[p] = rp;
-        }
-        const double a1 = n1[c];
-        if (a1 != 0.0) {
-          const double d = fma(-rp, rp, a1);
-          if (d <= tol3z * n2[c]) {
-            double s = 0.0;
-            for (int r = p + 1 + sub; r < N; r += kQuad) s += col[r] * col[r];
-            s = quad_sum(s, qmask);
-            if (sub == 0) { n1[c] = s; n2[c] = s; }
-          } else if (sub == 0) {
-            n1[c] = d;
-          }
+    const double* v = W + (long long)p * ldw;
+    // one thread per trailing column: each FP64 warp instruction then carries 32 columns'
+    // work, with no partial sums to combine (the FP64 pipe costs the same per warp
+    // instruction however many lanes are active)
+    for (int c = p + 1 + tid; c < N; c += kThreads) {
+      double* col = W + (long long)c * ldw;
+      double rp = col[p];
+      if (tp != 0.0) {
+        double dot = rp;   // v_p = 1
+        for (int r = p + 1; r < N; ++r) dot = fma(v[r], col[r], dot);
+        const double f = tp * dot;
+        for (int r = p + 1; r < N; ++r) col[r] = fma(-f, v[r], col[r]);
+        rp -= f;
+        col[p] = rp;
+      }
+      const double a1 = n1[c];
+      if (a1 != 0.0) {
+        const double d = fma(-rp, rp, a1);
+        if (d <= tol3z * n2[c]) {
+          double s = 0.0;
+          for (int r = p + 1; r < N; ++r) s = fma(col[r], col[r], s);
+          n1[c] = s;
+          n2[c] = s;
+        } else {
+          n1[c] = d;
         }
       }
     }
@@ -197,12 +198,12 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
 
   // outputs D and T = D^{-1} R P^T
   double* Db = D + (long long)b * N;
-  for (int r = tid; r < N; r += kThreads) Db[r] = fabs(W[(long long)r * N + r]);
+  for (int r = tid; r < N; r += kThreads) Db[r] = fabs(W[(long long)r * ldw + r]);
   double* Tb = Tp + (long long)b * NN;
   for (int e = tid; e < (int)NN; e += kThreads) {
     const int r = e / N, c = e - r * N;
-    const double d = fabs(W[r * N + r]);
-    Tb[r * N + perm[c]] = (c >= r) ? W[c * N + r] / d : 0.0;
+    const double d = fabs(W[(long long)r * ldw + r]);
+    Tb[r * N + perm[c]] = (c >= r) ? W[(long long)c * ldw + r] / d : 0.0;
   }
   __syncthreads();   // T and D are out: W's upper triangle is free
   // Q = H_0 H_1 ... H_{N-1} in place over W (column-major), by backward accumulation:
@@ -211,22 +212,18 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   // then turns column p (the reflector v, v_p = 1) into H_p e_p.
   for (int p = N - 1; p >= 0; --p) {
     const double tp = tau[p];
-    const double* v = W + (long long)p * N;
-    for (int c0 = p + 1; c0 < N; c0 += kColsPerPass) {
-      const int c = c0 + tid / kQuad;
-      if (c < N) {
-        double* col = W + (long long)c * N;
-        double dot = 0.0;
-        for (int r = p + 1 + sub; r < N; r += kQuad) dot += v[r] * col[r];
-        const double f = tp * quad_sum(dot, qmask);
-        if (f != 0.0)
-          for (int r = p + 1 + sub; r < N; r += kQuad) col[r] -= f * v[r];
-        __syncwarp(qmask);
-        if (sub == 0) col[p] = -f;
-      }
+    const double* v = W + (long long)p * ldw;
+    for (int c = p + 1 + tid; c < N; c += kThreads) {   // one thread per column, as above
+      double* col = W + (long long)c * ldw;
+      double dot = 0.0;
+      for (int r = p + 1; r < N; ++r) dot = fma(v[r], col[r], dot);
+      const double f = tp * dot;
+      if (f != 0.0)
+        for (int r = p + 1; r < N; ++r) col[r] = fma(-f, v[r], col[r]);
+      col[p] = -f;
     }
     __syncthreads();
-    double* cp = W + (long long)p * N;
+    double* cp = W + (long long)p * ldw;
     for (int r = tid; r < N; r += kThreads)
       cp[r] = r < p ? 0.0 : r == p ? 1.0 - tp : -tp * cp[r];
     __syncthreads();
@@ -235,7 +232,7 @@ k_qrp(const double* __restrict__ X, double* __restrict__ U, double* __restrict__
   double* Ub = U + (long long)b * NN;
   for (int e = tid; e < (int)NN; e += kThreads) {
     const int r = e / N, c = e - r * N;
-    Ub[e] = Q[c * N + r];
+    Ub[e] = Q[(long long)c * ldw + r];
   }
 }
 
@@ -313,7 +310,7 @@ k_solve(const double* __restrict__ X, const double* __restrict__ UR, long long s
 void qrp_udt(const double* X, double* U, double* D, double* Tp, double* ws, int N, int batch,
              cudaStream_t st) {
   const size_t small = (qrp_small_bytes(N) + 15) & ~(size_t)15;
-  const size_t big = small + (size_t)N * N * sizeof(double);
+  const size_t big = small + (size_t)N * (N + 1) * sizeof(double);   // W, ld N + 1
   const int use_smem = big <= kSmemLimit;
   const size_t bytes = use_smem ? big : small;
   allow_max_dynamic_smem((const void*)k_qrp);
