@@ -1,8 +1,8 @@
 """Oracle for the convolutional field generator. This is test infrastructure: only tests/,
 __graft_entry__.smoke() and bench.py's CPU legs may import it. Plain numpy, FP64.
 
-The generator is the network-initialization variant the survey of this project specifies
-beside the paper's own network (nimc.py): it maps noise z ~ N(0,1) of the field's shape
+The generator is a second network for the initialization step of network-initialized Monte
+Carlo, beside the paper's own network (nimc.py): it maps noise z ~ N(0,1) of the field's shape
 (L_tau x Lx x Ly, one channel) to independent Bernoulli logits, one per field entry s(i, l),
 through four periodic 3D convolutions with 3 x 3 x 3 kernels:
 

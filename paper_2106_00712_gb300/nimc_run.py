@@ -175,11 +175,11 @@ def run_ml(n_fields=20000, every=10, warm=100, chains=256, channels=32, epochs=3
     1. training fields: `chains` DQMC chains (SPLIT_BF16) from random fields, `warm` sweeps,
        then one field per chain every `every` sweeps until n_fields are collected;
     2. maximum-likelihood training (Adam, lr, batches of `batch` fields with fresh noise);
-    3. the judge: n_gen chains from generated fields and n_gen from random fields, per-sweep
-       means of E and D, and the first sweep from which each stays at equilibrium (the
-       reference: a long run of random starts).
+    3. the thermalization test: n_gen chains from generated fields and n_gen from random
+       fields, per-sweep means of E and D, and the first sweep from which each stays at
+       equilibrium (the reference: a long run of random starts).
     With noise independent of the fields the likelihood's optimum is a constant logit per
-    entry, the log-odds of its mean occupation (oracle.cgen.optimal_bias), so the judge is
+    entry, the log-odds of its mean occupation (oracle.cgen.optimal_bias), so the test is
     expected to find generated starts no better than random ones; the run measures it, with
     a second set of random starts (another seed) to show how far the convergence sweep moves
     between two draws of one start distribution."""
