@@ -323,6 +323,22 @@ def probe_peaks(nmc, torch, stream):
                 b.synchronize()
                 best = min(best, a.elapsed_time(b))
             out[name] = blocks * threads * iters * 16.0 / (best * 1e-3) / 1e12
+            if kind == 0:
+                # the same warp instructions on one lane per warp (kind 2): the FP64 pipe's
+                # cost per warp instruction whatever the active lanes
+                best1 = float("inf")
+                for _ in range(3):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    nmc.nmc_fma_probe(2, blocks, threads, iters, buf.data_ptr(),
+                                      stream.cuda_stream)
+                    b.record(stream)
+                    b.synchronize()
+                    best1 = min(best1, a.elapsed_time(b))
+                warp_instr = blocks * (threads // 32) * iters * 8.0
+                out["fp64_warp_dfma_per_s_32_lanes"] = warp_instr / (best * 1e-3)
+                out["fp64_warp_dfma_per_s_1_lane"] = warp_instr / (best1 * 1e-3)
         except Exception:
             out[name] = NOMINAL_TFLOPS[name]
             out[name + "_source"] = "nominal (probe failed)"

@@ -323,7 +323,10 @@ nmc_status nmc_green_noalloc(int N, int L_tau, int n_wrap, double lam, const dou
  * or FP32 (kind 1), and store one value per thread to d_out (device, blocks * threads
  * elements of that type). Work: blocks * threads * iters * 16 flop. Timed by the caller
  * with events on the same stream, it gives the measured FP64 / FP32 SIMT peak that the
- * roofline of the SIMT kernels is quoted against. NMC_EINVAL for bad sizes. */
+ * roofline of the SIMT kernels is quoted against. Kinds 2 (FP64) and 3 (FP32) run the same
+ * loop on one lane per warp only: the same warp instructions with 1/32 of the work, which
+ * shows whether a pipe's cost is per warp instruction or per active lane. NMC_EINVAL for
+ * bad sizes. */
 nmc_status nmc_fma_probe(int kind, int blocks, int threads, int iters, void* d_out,
                          void* cuda_stream);
 
