@@ -260,6 +260,7 @@ struct TcGeom {
   int NT, KC, KP, n_chunks, n_tiles;
   long long rows;     // batch * N
   int* err;           // device error flag (bounded waits)
+  int rpt;            // rows of the chain operand per tile (<= 128; the rest of the tile is zero)
 };
 
 // Shared memory (bytes, from a 1024-aligned base): two stages of A slices
@@ -325,8 +326,8 @@ __global__ void __launch_bounds__(SL + 32, SL == 512 ? 1 : 2)
   // contiguous runs of its rows and writes their 16-byte slice pieces contiguously
   const int r = (warp * (32 / kKParts) + lane / kKParts) & (kM - 1), kp = lane & (kKParts - 1);
   const bool kpart = !mma_warp && kp * 8 < KC;   // KC = 16: only two K groups per chunk
-  const long long grow = (long long)blockIdx.x * kM + r;
-  const bool valid = grow < geo.rows;
+  const long long grow = (long long)blockIdx.x * geo.rpt + r;
+  const bool valid = r < geo.rpt && grow < geo.rows;
   const int b = valid ? (int)(grow / N) : 0;
   const int i = valid ? (int)(grow % N) : 0;
   const df2* X = CONST_A ? g.B + (long long)b * g.sB : g.A + (long long)b * g.sA;
@@ -440,7 +441,9 @@ __global__ void __launch_bounds__(SL + 32, SL == 512 ? 1 : 2)
       const int st = kc & 1, use = kc >> 1;
       if (kc >= 2)   // this stage's previous MMAs (chunk kc - 2) have completed
         ok = mbar_wait(&bar_mma[st], (use - 1) & 1, geo.err, 1) && ok;
-      if (kpart) {
+      // rows past the tile's (or the operand's) end are left unsliced: each output row of the
+      // MMA depends on its own A row only, and the epilogue discards those rows
+      if (kpart && valid) {
         df2 v[8];
         if (cache) {
 #pragma unroll
@@ -469,8 +472,8 @@ __global__ void __launch_bounds__(SL + 32, SL == 512 ? 1 : 2)
     const int c0 = cq * 16;
     if (c0 < NT) {
       const int re = lq * 32 + lane;   // the tile row of this lane
-      const long long grow_e = (long long)blockIdx.x * kM + re;
-      const bool valid_e = grow_e < geo.rows;
+      const long long grow_e = (long long)blockIdx.x * geo.rpt + re;
+      const bool valid_e = re < geo.rpt && grow_e < geo.rows;
       const int be = valid_e ? (int)(grow_e / N) : 0;
       const int ie = valid_e ? (int)(grow_e % N) : 0;
       const int sge = (g.ns == 2 && (be & 1)) ? -1 : 1;
@@ -632,18 +635,49 @@ bool tc_prepare_const(const double* M, int N, int as_b, void* slices, int* exps,
   return r == CUDA_SUCCESS;
 }
 
+// The SMs of the current device (cached per device)
+int sm_count() {
+  static std::mutex mu;
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+// Rows per tile: kM, unless the grid takes several waves of `slots` resident CTAs; then the
+// fewest rows that still fill those waves, so that the last wave is not a partial one (the
+// slicing and the epilogue, which bound the kernel, scale with a tile's rows).
+int balanced_rows_per_tile(long long rows, int n_col_tiles, int slots) {
+  const long long tiles = ((rows + kM - 1) / kM) * n_col_tiles;
+  const long long waves = (tiles + slots - 1) / slots;
+  if (waves < 2 || slots < 1) return kM;
+  const long long row_tiles = waves * slots / n_col_tiles;
+  const long long rpt = (rows + row_tiles - 1) / row_tiles;
+  return (int)(rpt < 1 ? 1 : rpt > kM ? kM : rpt);
+}
+
 void gemm_tc(const DfGemmArgs& g, bool const_is_a, const void* tmap, int* err,
              cudaStream_t st) {
   if (g.batch <= 0) return;
   const TcShape s = tc_shape(g.N);
-  TcGeom geo{s.NT, s.KC, s.KP, s.n_chunks, s.n_tiles, (long long)g.batch * g.N, err};
+  TcGeom geo{s.NT, s.KC, s.KP, s.n_chunks, s.n_tiles, (long long)g.batch * g.N, err, kM};
   // Tensor memory holds 512 columns per SM: request enough shared memory that no more CTAs
   // share an SM than their accumulators fit (228 KB per SM, 1 KB reserved per CTA).
   const int cols = (int)tmem_columns(kAcc * s.NT);
   const size_t fit = 233472 / (512 / cols + 1) - 1024 + 16;
   size_t smem = (size_t)2 * (a_bytes(s.KC) + b_bytes(s.NT, s.KC)) + 1024;
   if (smem < fit) smem = fit;
-  const dim3 grid((unsigned)((geo.rows + kM - 1) / kM), (unsigned)s.n_tiles);
+  geo.rpt = balanced_rows_per_tile(geo.rows, s.n_tiles, sm_count() * (512 / cols));
+  const dim3 grid((unsigned)((geo.rows + geo.rpt - 1) / geo.rpt), (unsigned)s.n_tiles);
   const CUtensorMap& m = *(const CUtensorMap*)tmap;
   auto run = [&](auto kernel, int threads) {
     allow_max_dynamic_smem((const void*)kernel);
