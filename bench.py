@@ -69,7 +69,7 @@ TRAFFIC = {
     # read, 0 written; on the right 18.22 MB read, 1.35 MB written -- the chain operand
     # (16.78 MB as FP32 pairs) once plus the constant's slices; weighted by the sweep's launch
     # mix (84 : 44)
-    "gemm_tc.cu": ("88b2562038f38ec8", 17.83e6),
+    "gemm_tc.cu": ("306943109b105476", 17.83e6),
     # k_flip_df<false> (the FP32-pipe fold used at N = 64), same configuration (one slice of
     # 256 chains x 2 spins): 16.89 MB read (G as FP32 pairs, once), 0 written (stays in L2)
     "flip.cu": ("a6c5108ea7f07fd0", 16.89e6),
@@ -587,7 +587,8 @@ def main():  # noqa: C901
     rl = class_rooflines(st, base, ns, r["obs"].accept, peaks, prec == 2)
     roofline = dict(rl.get(dom) or rl[max(rl, key=lambda k: st[k][2])])
     roofline.update({"dominant_class": dom, "share": share})
-    roofline["others"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "frac")}
+    roofline["others"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "frac",
+                                                  "traffic", "hbm_gbs", "hbm_frac") if kk in v}
                           for k, v in rl.items() if k != dom}
     sf = step_flop(WL.N, WL.L_tau, WL.L_tau // WL.n_wrap, WL.n_chains, ns, r["obs"].accept)
     whole_step = {"algorithmic_tflop_per_step": sf / 1e12,

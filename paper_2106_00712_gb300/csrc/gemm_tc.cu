@@ -635,28 +635,10 @@ bool tc_prepare_const(const double* M, int N, int as_b, void* slices, int* exps,
   return r == CUDA_SUCCESS;
 }
 
-// The SMs of the current device (cached per device)
-int sm_count() {
-  static std::mutex mu;
-  static int cached[64] = {0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-  std::lock_guard<std::mutex> lock(mu);
-  if (cached[dev] == 0) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
-      cudaGetLastError();
-      n = 1;
-    }
-    cached[dev] = n;
-  }
-  return cached[dev];
-}
-
 // Rows per tile: kM, unless the grid takes several waves of `slots` resident CTAs; then the
 // fewest rows that still fill those waves, so that the last wave is not a partial one (the
 // slicing and the epilogue, which bound the kernel, scale with a tile's rows).
-int balanced_rows_per_tile(long long rows, int n_col_tiles, int slots) {
+static int balanced_rows_per_tile(long long rows, int n_col_tiles, int slots) {
   const long long tiles = ((rows + kM - 1) / kM) * n_col_tiles;
   const long long waves = (tiles + slots - 1) / slots;
   if (waves < 2 || slots < 1) return kM;

@@ -210,6 +210,8 @@ size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem, int ns);
 // ---------------------------------------------------------------------------- misc
 // Raise a kernel's dynamic shared-memory limit to the device maximum (once per device).
 void allow_max_dynamic_smem(const void* func);
+// The SMs of the current device (cached per device; 1 if the query fails)
+int sm_count();
 // Prefer the largest shared-memory carveout for a kernel (once per device), so that several
 // of its CTAs fit on an SM.
 void prefer_max_shared_carveout(const void* func);
