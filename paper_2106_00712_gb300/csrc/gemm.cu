@@ -245,23 +245,8 @@ k_gemm_pair(const GemmArgs<double> g) {
   fold_drift_max(g, b, dmax);
 }
 
-// Fill of the last round of CTAs when `ctas` equal CTAs share `sms` SMs: each SM's time
-// grows with the CTAs it is given (they share its pipes), so the grid takes
-// ceil(ctas / sms) CTA-times while the average SM needs ctas / sms.
-double sm_fill(long long ctas, int sms) {
-  const long long per = (ctas + sms - 1) / sms;
-  return per > 0 ? (double)ctas / ((double)per * sms) : 1.0;
-}
-
-// 64 x 64 tiles, unless 32 x 32 tiles fill the SMs markedly better (many small products:
-// 512 products of 64 x 64 are 512 CTAs, 3.4 per SM, so a quarter of the SMs hold four and
-// set the time; as 2048 CTAs of 32 x 32 they spread to within one small CTA)
 bool use_tiles_64(const GemmArgs<double>& g, int mx) {
-  if (mx < 48) return false;
-  const int sms = sm_count();
-  const long long c64 = (long long)((g.N + 63) / 64) * ((g.M + 63) / 64) * g.batch;
-  const long long c32 = (long long)((g.N + 31) / 32) * ((g.M + 31) / 32) * g.batch;
-  return sm_fill(c32, sms) < sm_fill(c64, sms) + 0.05;
+  return mx >= 48 && prefer_tiles_64(g.M, g.N, g.batch);
 }
 bool use_tiles_64(const GemmArgs<float>&, int mx) { return mx >= 48; }
 

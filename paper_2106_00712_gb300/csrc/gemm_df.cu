@@ -112,7 +112,7 @@ __global__ void k_split(const double* x, df2* y, long long n) {
 void gemm_df(const DfGemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   const int mx = g.M > g.N ? g.M : g.N;
-  if (mx >= 48) {
+  if (mx >= 48 && prefer_tiles_64(g.M, g.N, g.batch)) {
     dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.batch);
     k_gemm_df<64, 64, 16, 4, 4><<<grid, 256, 0, st>>>(g);
   } else if (mx >= 24) {

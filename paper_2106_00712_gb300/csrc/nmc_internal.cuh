@@ -212,6 +212,23 @@ size_t flip_smem_bytes(int N, int kk, size_t elem, int g_in_smem, int ns);
 void allow_max_dynamic_smem(const void* func);
 // The SMs of the current device (cached per device; 1 if the query fails)
 int sm_count();
+// Fill of the last round of CTAs when `ctas` equal CTAs share `sms` SMs: each SM's time grows
+// with the CTAs it is given (they share its pipes), so the grid takes ceil(ctas / sms)
+// CTA-times while the average SM needs ctas / sms.
+inline double sm_fill(long long ctas, int sms) {
+  const long long per = (ctas + sms - 1) / sms;
+  return per > 0 ? (double)ctas / ((double)per * sms) : 1.0;
+}
+// 64 x 64 output tiles for an M x N product batch, unless 32 x 32 tiles fill the SMs markedly
+// better (many small products: 512 products of 64 x 64 are 512 CTAs, 3.4 per SM, so a quarter
+// of the SMs hold one more than the rest and set the time; 2048 CTAs of 32 x 32 spread to
+// within one small CTA)
+inline bool prefer_tiles_64(int M, int N, int batch) {
+  const int sms = sm_count();
+  const long long c64 = (long long)((N + 63) / 64) * ((M + 63) / 64) * batch;
+  const long long c32 = (long long)((N + 31) / 32) * ((M + 31) / 32) * batch;
+  return sm_fill(c32, sms) < sm_fill(c64, sms) + 0.05;
+}
 // Prefer the largest shared-memory carveout for a kernel (once per device), so that several
 // of its CTAs fit on an SM.
 void prefer_max_shared_carveout(const void* func);
