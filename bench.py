@@ -69,7 +69,7 @@ TRAFFIC = {
     # read, 0 written; on the right 18.22 MB read, 1.35 MB written -- the chain operand
     # (16.78 MB as FP32 pairs) once plus the constant's slices; weighted by the sweep's launch
     # mix (84 : 44)
-    "gemm_tc.cu": ("306943109b105476", 17.83e6),
+    "gemm_tc.cu": ("57ee5e38a167fac9", 17.83e6),
     # k_flip_df<false> (the FP32-pipe fold used at N = 64), same configuration (one slice of
     # 256 chains x 2 spins): 16.89 MB read (G as FP32 pairs, once), 0 written (stays in L2)
     "flip.cu": ("a6c5108ea7f07fd0", 16.89e6),

@@ -19,7 +19,8 @@
 // pairs, and scales by 2^{e_row + f_col}.
 //
 // Matrix shapes: all batch x N rows of the chain operand are one long M dimension (the
-// constant is shared), cut into tiles of 128 rows (one tensor-memory lane per row); the
+// constant is shared), cut into tiles of at most 128 rows (one tensor-memory lane per row;
+// fewer when that fills every wave of a multi-wave grid, balanced_rows_per_tile); the
 // output columns are cut into tiles of NT <= 64 (seven accumulators x NT columns of tensor
 // memory), K into chunks of KC = 32 (16 for N <= 16). One CTA of 544 threads per (row
 // tile, column tile), one CTA per SM: 16 warps slice the chain operand's rows into two
