@@ -288,6 +288,39 @@ def test_fast_update_and_wrap_equal_direct_inversion():
         assert np.max(np.abs(ch.G[a] - dqmc.green_naive(ch.P, ch.s, sigma, 2))) < 1e-10
 
 
+def test_qrp_udt_is_a_pivoted_udt_decomposition():
+    """The stabilization's decomposition M = U diag(D) T against its definition (reading R6),
+    on columns graded over 24 decades as a UDV chain makes them: U orthogonal, D the moduli
+    of R's diagonal in non-increasing order (column pivoting), T P upper triangular with a
+    unit-modulus diagonal, the product reconstructing M column by column, and the first
+    pivot the column of largest norm (ties to the lowest index, checked on an exact tie)."""
+    rng = np.random.default_rng(7)
+    N = 24
+    M = rng.normal(size=(N, N)) * np.logspace(-12, 12, N)[rng.permutation(N)][None, :]
+    U, D, T = dqmc.qrp_udt(M)
+    assert np.max(np.abs(U.T @ U - np.eye(N))) < 1e-13
+    assert np.all(D > 0) and np.all(np.diff(D) <= 0)
+    # T's column order: T P = R / D is upper triangular with |diagonal| = 1, so pivot k is
+    # the column whose last nonzero entry is in row k
+    norms = np.linalg.norm(M, axis=0)
+    last = [int(np.nonzero(T[:, c])[0].max()) for c in range(N)]
+    assert sorted(last) == list(range(N))
+    piv = [last.index(k) for k in range(N)]
+    TP = T[:, piv]
+    assert np.max(np.abs(np.tril(TP, -1))) == 0.0
+    assert np.allclose(np.abs(np.diag(TP)), 1.0, atol=1e-12)
+    assert piv[0] == int(np.argmax(norms))
+    rec = U @ (D[:, None] * T)
+    assert np.max(np.abs(rec - M) / norms[None, :]) < 1e-13
+    # an exact tie of the largest norms (both exactly 5) goes to the lower index
+    Mt = rng.normal(size=(6, 6)) * 0.1
+    Mt[:, 1] = [3.0, 4.0, 0.0, 0.0, 0.0, 0.0]
+    Mt[:, 4] = [0.0, 0.0, 5.0, 0.0, 0.0, 0.0]
+    _, Dt, Tt = dqmc.qrp_udt(Mt)
+    assert Dt[0] == 5.0
+    assert abs(abs(Tt[0, 1]) - 1.0) < 1e-15 and np.all(Tt[1:, 1] == 0.0)
+
+
 def test_stabilized_green_vs_scratch_and_naive():
     """Stack-recomputed G agrees with a from-scratch stabilized product (8x8, beta=4,
     cond(A) ~ 1e9) and with direct inversion at small beta."""
